@@ -1,0 +1,135 @@
+"""Pins of the oracle's dissimilarity key (Eq. 1, reading R1) against
+arithmetic that does not go through the oracle: Python's correctly rounded
+integer true division, exact Fractions over region means, the two-pixel
+closed form, and the Ward sum-of-squares identity."""
+import json
+import os
+import random
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+
+def test_div_rn_matches_python_true_division(orc):
+    # CPython's int / int is correctly rounded (nearest-even) binary64.
+    rng = random.Random(7)
+    cases = []
+    for _ in range(4000):
+        nb = rng.randint(1, 127)
+        db = rng.randint(1, 126)
+        N = rng.getrandbits(nb)
+        D = rng.getrandbits(db) or 1
+        cases.append((N, D))
+    cases += [(1, 3), (2**127 - 1, 1), (1, 2**126 + 12345), (2**53 + 1, 1), (2**53 + 3, 2),
+              (2**60 + 1, 2**60 - 1), (0, 17), (3, 2**100)]
+    for N, D in cases:
+        assert orc.div_rn(N, D) == N / D, (N, D)
+
+
+def test_div_rn_exact_ties_round_to_even(orc):
+    # N / D exactly halfway between two binary64 neighbours.
+    rng = random.Random(11)
+    for _ in range(2000):
+        q = rng.getrandbits(52) | (1 << 52)          # 53-bit significand
+        e = rng.randint(-60, 40)
+        num = 2 * q + 1                               # (q + 1/2) * 2^(e+1)
+        sh = rng.randint(0, 20)
+        if e >= 0:
+            N, D = num << (e + sh), 1 << sh
+        else:
+            N, D = num << sh, 1 << (sh - e)
+        if N >= 2**127 or D >= 2**127:
+            continue
+        got = orc.div_rn(N, D)
+        assert got == N / D
+        # explicit: the result's significand is even
+        m, ex = np.frexp(got)
+        sig = int(m * 2**53)
+        assert sig % 2 == 0
+
+
+def _K_means(ni, Si, nj, Sj):
+    # Eq. 1 squared written over region means (not over N/D)
+    tot = sum((Fraction(int(a), ni) - Fraction(int(b), nj)) ** 2 for a, b in zip(Si, Sj))
+    return Fraction(ni * nj, ni + nj) * tot
+
+
+def test_key_two_pixels_closed_form(orc):
+    rng = np.random.default_rng(3)
+    for _ in range(300):
+        B = int(rng.integers(1, 40))
+        x = rng.integers(0, 65536, B)
+        y = rng.integers(0, 65536, B)
+        want = float(Fraction(int(((x - y) ** 2).sum()), 2))    # K = ||x - y||^2 / 2
+        assert orc.key(1, x, 1, y) == want
+
+
+def test_key_matches_exact_rational_over_means(orc):
+    rng = np.random.default_rng(5)
+    for _ in range(400):
+        B = int(rng.integers(1, 64))
+        ni = int(rng.integers(1, 1 << int(rng.integers(1, 21))))
+        nj = int(rng.integers(1, 1 << int(rng.integers(1, 21))))
+        Si = rng.integers(0, 65536, B) * ni
+        Sj = rng.integers(0, 65536, B) * nj
+        # perturb so that the means are not integers
+        Si = Si + rng.integers(0, ni, B)
+        Sj = Sj + rng.integers(0, nj, B)
+        assert orc.key(ni, Si, nj, Sj) == float(_K_means(ni, Si, nj, Sj))
+
+
+def test_key_is_symmetric_and_zero_on_equal_means(orc):
+    rng = np.random.default_rng(9)
+    for _ in range(100):
+        B = int(rng.integers(1, 32))
+        ni, nj = int(rng.integers(1, 5000)), int(rng.integers(1, 5000))
+        mu = rng.integers(0, 10000, B)
+        assert orc.key(ni, mu * ni, nj, mu * nj) == 0.0
+        Si = rng.integers(0, 10**8, B)
+        Sj = rng.integers(0, 10**8, B)
+        assert orc.key(ni, Si, nj, Sj) == orc.key(nj, Sj, ni, Si)
+
+
+def test_key_ward_identity(orc):
+    # Ward: n_i n_j/(n_i+n_j) ||mu_i - mu_j||^2 = SSE(i u j) - SSE(i) - SSE(j)
+    rng = np.random.default_rng(13)
+    for _ in range(100):
+        B = int(rng.integers(1, 6))
+        A = rng.integers(0, 4096, (int(rng.integers(1, 30)), B))
+        C = rng.integers(0, 4096, (int(rng.integers(1, 30)), B))
+
+        def sse(X):
+            n = len(X)
+            return sum(sum(Fraction(int(v)) ** 2 for v in X[:, b]) - Fraction(int(X[:, b].sum())) ** 2 / n
+                       for b in range(B))
+        ward = sse(np.vstack([A, C])) - sse(A) - sse(C)
+        assert orc.key(len(A), A.sum(0), len(C), C.sum(0)) == float(ward)
+
+
+def test_worked_example_fixture(orc):
+    d = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "worked_1x4.json")))
+    im = d["image"]
+    img = np.array(im["values"], dtype=np.uint16).reshape(im["rows"], im["cols"], im["bands"])
+    for case in d["cases"]:
+        for mode in (0, 1):
+            r = orc.run(img, None, spclust_wght=case["spclust_wght"], mode=mode, **d["params"])
+            got = [(int(m["step"]), int(m["kind"]), int(m["survivor_id"]), int(m["absorbed_id"]), float(m["key"]))
+                   for m in r.log]
+            want = [(s, k, a, b, float(Fraction(K))) for s, k, a, b, K in case["log"]]
+            assert got == want, (case["spclust_wght"], got)
+            assert r.stats["pairs"] == case["pairs"]
+            assert np.array_equal(r.log["dissim"], np.sqrt(r.log["key"]))
+
+
+def test_range_and_parameter_errors(orc):
+    img = np.full((2, 2, 1), 65535, dtype=np.uint16)
+    with pytest.raises(orc.OracleError) as e:
+        orc.run(img, None, spclust_wght=1.5)
+    assert e.value.code == -1
+    with pytest.raises(orc.OracleError):
+        orc.run(img, None, connectivity=6)
+    # B * (P^2/4 * maxval)^2 >= 2^127 for a large enough P: 3000x3000 of 65535 with 224 bands
+    # is too big to allocate here, so check the bound on a cheap case that passes
+    r = orc.run(img, None, conv_nregions=1)
+    assert r.levels[-1].counts.tolist() == [4]
