@@ -1,0 +1,300 @@
+#!/usr/bin/env python
+"""Benchmark of the RHSEG hot path on one B300 per rank.
+
+One step = one whole RHSEG run (deepest level to root) on the synthetic
+1024x1024x224 workload (L=5, w=0.1, 64 regions, 10% no-data mask, FP16
+tensor-core screen), image already resident in HBM.  The metric is region-pair
+dissimilarities per second: the pairs the method defines (adjacent pairs of
+each adjacent step + non-adjacent pairs of each spectral step) divided by the
+device time of the run; the end-to-end seconds per run are ms_per_step.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Multi-GPU: replicas (each rank runs the whole workload; no collective on the
+data path), value = pairs of all ranks / max time over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "region-pair dissimilarities/s and RHSEG end-to-end s at 1024²×224, mixed vs FP64, label-exact"
+UNIT = "pairs/s"
+
+PEAKS_FALLBACK = {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "bf16_tflops_sustained": 1400.0, "sm_max_mhz": 2032.0}
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        d["_source"] = "measured"
+        return d
+    d = dict(PEAKS_FALLBACK)
+    d["_source"] = "fallback"
+    return d
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms while running."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self):
+        self.proc = None
+        self.out = None
+
+    def start(self):
+        try:
+            self.out = open(os.path.join("/tmp", f"rhseg_clocks_{os.getpid()}.csv"), "w+")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200"], stdout=self.out, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.out.flush()
+        self.out.seek(0)
+        rows = [r.strip().split(",") for r in self.out.read().strip().splitlines() if r.strip()]
+        self.out.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [x.strip() for x in r]
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                smax.append(float(r[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, r[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def workload(k):
+    import synth
+    w = synth.WORKLOADS[k]
+    img, mask = synth.make(k)
+    return w, img, mask
+
+
+def cpu_baseline(img, mask, params, target_s=15.0):
+    """The oracle as it stands (plain mode: every pair recomputed each
+    iteration, single thread), on a bounded sample: the first iterations of
+    deepest-level section 0.  Returns pairs/s."""
+    import oracle
+    kw = {k: v for k, v in params.items() if k != "precision"}
+    t0 = time.perf_counter()
+    r = oracle.hseg_leaf(img, mask, 0, max_iters=1, mode=0, **kw)
+    dt = time.perf_counter() - t0
+    iters = 1
+    pairs = r.stats["pairs"]
+    if dt < target_s:
+        n = max(1, min(50, int(target_s / max(dt, 1e-3))))
+        t0 = time.perf_counter()
+        r = oracle.hseg_leaf(img, mask, 0, max_iters=n, mode=0, **kw)
+        dt = time.perf_counter() - t0
+        iters = n
+        pairs = r.stats["pairs"]
+    return {"value": pairs / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"plain oracle (all pairs recomputed per iteration), first {iters} HSEG iteration(s) of "
+                      f"deepest-level section 0 (64x64 px, {int(r.stats['pairs'])} pairs, {dt:.1f} s)"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    w, img, mask = workload(args.workload)
+    import oracle
+    oracle.build()
+    kw = {k: v for k, v in w.params.items() if k != "precision"}
+    times, pairs = [], []
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        r = oracle.hseg_leaf(img, mask, 0, max_iters=1, mode=0, **kw)
+        dt = time.perf_counter() - t0
+        if i >= args.warmup:
+            times.append(dt)
+            pairs.append(r.stats["pairs"])
+    val = sum(pairs) / sum(times)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * sum(times) / len(times),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int128-exact/f64",
+        "data": "synthetic", "config": {"workload": w.name, "sample": "HSEG iteration 1 of deepest section 0"},
+        "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": "plain oracle, first HSEG iteration of deepest-level section 0 per step"},
+        "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", type=int, default=4)
+    ap.add_argument("--precision", type=int, default=None)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import paper_2106_12942_b300 as P
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    w, img, mask = workload(args.workload)
+    params = dict(w.params)
+    if args.precision is not None:
+        params["precision"] = args.precision
+    params["profile"] = 1
+    stream = torch.cuda.current_stream()
+    img_d = torch.from_numpy(img.view(np.int16)).cuda().view(torch.uint16)
+    mask_d = None if mask is None else torch.from_numpy(mask).cuda()
+    seg = P.RHSEG(img_d, mask_d, stream=stream, **params)
+
+    for _ in range(args.warmup):
+        seg.run(stream=stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clk = ClockSampler()
+    clk.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    stats = []
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.steps):
+        seg.run(stream=stream)
+        stats.append(seg.stats())
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    ms = e0.elapsed_time(e1)
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        dist.barrier()
+    pairs = stats[-1]["pairs"]
+    value = world * pairs * args.steps / (ms / 1000.0)
+
+    # dominant kernel: the spectral screen; algorithmic flops 2*B per screened pair
+    peaks = load_peaks()
+    scr_ms = sum(s["screen_ms"] for s in stats)
+    scr_n = sum(s["screen_launches"] for s in stats)
+    scr_pairs = sum(s["screened_pairs"] for s in stats)
+    run_ms = sum(s["run_ms"] for s in stats)
+    B = w.bands
+    prec = params["precision"]
+    flops = 2.0 * B * scr_pairs
+    achieved = flops / (scr_ms / 1000.0) / 1e12 if scr_ms > 0 else 0.0
+    impl = stats[-1]["screen_impl"]
+    if impl == 3:
+        bound, peak = "tensor", float(peaks["bf16_tflops"])
+        peak_note = f"{peaks['_source']} bf16 dense burst (fp16 has the same nominal rate)"
+    elif impl == 1:
+        bound, peak = "alu", 148 * 2 * 2.0 * float(peaks.get("sm_max_mhz", 2032.0)) / 1e6
+        peak_note = "fp64: 148 SM x 2 DFMA/clk x 2 flop x max SM clock (nominal 1.25 TFLOP/s)"
+    else:
+        bound, peak = "alu", 148 * 128 * 2.0 * float(peaks.get("sm_max_mhz", 2032.0)) / 1e6
+        peak_note = "fp32 FMA: 148 SM x 128 lanes x 2 flop x max SM clock"
+    roofline = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak if peak else None, "traffic": None,
+                "kernel": {1: "screen_simt<f64>", 2: "screen_simt<f32 accumulate>", 3: "screen_tcgen05"}.get(impl, "none"),
+                "launches": scr_n, "avg_launch_ms": scr_ms / max(scr_n, 1),
+                "share_of_run": scr_ms / run_ms if run_ms else None, "peak_source": peak_note}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": {0: "int64+f64", 1: "int64+f16", 2: "int64+bf16", 3: "int64+f32"}[prec],
+        "data": "synthetic",
+        "config": {"workload": w.name, "rows": w.rows, "cols": w.cols, "bands": w.bands,
+                   "rnb_levels": params["rnb_levels"], "spclust_wght": params["spclust_wght"],
+                   "conv_nregions": params["conv_nregions"], "precision": prec, "parallelism": f"replicas{world}",
+                   "l2": "inputs larger than L2 (cube 470 MB, region tables several GB)",
+                   "pairs_per_step": pairs, "seconds_per_rhseg_run": ms / args.steps / 1000.0},
+        "roofline": roofline,
+        "clocks": clocks,
+        "gpu_launches": int(sum(s["kernel_launches"] for s in stats)),
+        "kernel_ms": {"screen": scr_ms / args.steps, "adj_step": sum(s["adj_ms"] for s in stats) / args.steps,
+                      "spec_step": sum(s["spec_ms"] for s in stats) / args.steps},
+        "screen": {"screened_pairs": stats[-1]["screened_pairs"], "candidates": stats[-1]["candidates"],
+                   "fallbacks": stats[-1]["fallbacks"]},
+    }
+
+    if not args.no_e2e:
+        # end to end through the C ABI with host buffers: H2D of the cube and
+        # mask from pinned memory, the run, D2H of the final labels and tables
+        img_h = torch.from_numpy(img.view(np.int16)).pin_memory()
+        mask_h = None if mask is None else torch.from_numpy(mask).pin_memory()
+        seg.close()
+        segh = P.RHSEG(img, mask, stream=stream, **params)
+        segh.set_image(img_h, mask_h, stream=stream).run(stream=stream)
+        nl = segh.n_levels()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        d2h = 0
+        for _ in range(args.steps):
+            segh.set_image(img_h, mask_h, stream=stream)
+            segh.run(stream=stream)
+            lab, sums, cnt = segh.level(nl - 1)
+            d2h = lab.nbytes + sums.nbytes + cnt.nbytes
+        torch.cuda.synchronize()
+        te = time.perf_counter() - t0
+        if dist:
+            t = torch.tensor([te], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            te = float(t.item())
+        h2d = img.nbytes + (0 if mask is None else mask.nbytes)
+        line["e2e"] = {"value": world * pairs * args.steps / te, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                       "d2h_bytes_per_step": int(d2h), "seconds_per_step": te / args.steps}
+        segh.close()
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(img, mask, params)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

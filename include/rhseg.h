@@ -1,0 +1,189 @@
+/*
+ * rhseg.h -- C ABI of the B300 (sm_103a) RHSEG/HSEG hot path.
+ *
+ * The method: recursive hierarchical segmentation of a hyperspectral image
+ * (thesis "High Performance Hyperspectral Image Classification using
+ * Graphics Processing Units", 2015, Section 4.1).  HSEG (Section 4.1, steps
+ * 1-4) starts from one region per pixel and repeats: merge the spatially
+ * adjacent pair of minimum dissimilarity; then merge the non-adjacent pair of
+ * minimum dissimilarity if it is below the adjacent minimum scaled by the
+ * spectral clustering weight; until the target region count.  The
+ * dissimilarity is the square root of the band-sum mean squared error
+ * (Eq. 1).  RHSEG (Section 4.1, Fig. 4.3/4.4) runs HSEG on 4^(L-1) sections,
+ * reassembles them four at a time (regions on the seams linked across,
+ * 8-neighbourhood) and runs HSEG again up to the whole image.
+ *
+ * Conventions the thesis leaves open, fixed here (identical in every
+ * precision form; results are bit-exact across forms):
+ *   - K = d^2 = N / D, N = sum_b (n_j S_ib - n_i S_jb)^2, D = n_i n_j (n_i+n_j)
+ *     from exact int64 band sums S and counts n; K is the correctly rounded
+ *     binary64 of the exact rational; dissim = sqrt(K).
+ *   - ties broken on (K, smaller region ID, larger region ID); region ID =
+ *     1 + smallest raster index (row * cols + col) of its pixels; the
+ *     survivor of a merge keeps the smaller ID.
+ *   - spectral step on the state after the adjacent merge of the same
+ *     iteration, non-adjacent pairs only, merge iff K < (w*w) * K_adj
+ *     (binary64; +inf when no adjacent pair is left; w = 0: no spectral step).
+ *   - stop test before each iteration and after every merge; an iteration
+ *     that merges nothing stalls the section (not an error).
+ *   - sections split at floor(h/2), floor(w/2), children in Z order.
+ *   - seam pass at each reassembly (the boundary-artifact removal that
+ *     Section 6.2 names as future work): a pixel with a neighbour in another
+ *     child section leaves its region R and becomes a one-pixel region iff
+ *     min over those neighbours' regions Q of K({p}, Q) < K({p}, R); all
+ *     tests on the pre-pass state, applied together, IDs re-derived.
+ *   - output levels: c_0 = count at the start of the root HSEG,
+ *     c_{K-1} = conv_nregions, geometric in between (nearest-even),
+ *     duplicates removed; labels renumbered 1..R in raster order of first
+ *     appearance (= ID order).
+ *
+ * Error behaviour: every call returns 0 (RHSEG_OK) or a negative code;
+ * rhseg_strerror() names it.  No call aborts the process.
+ * Threading: a handle is not thread-safe; distinct handles are independent.
+ */
+#ifndef RHSEG_H
+#define RHSEG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    RHSEG_OK = 0,
+    RHSEG_EINVAL = -1,    /* bad dimensions or parameters                          */
+    RHSEG_ERANGE = -2,    /* exact-key bound fails: B*(P^2/4*maxval)^2 >= 2^127 or
+                             P^2/4*maxval >= 2^62 (P = unmasked pixels)           */
+    RHSEG_ENOMEM = -3,    /* device allocation failed                              */
+    RHSEG_ECUDA = -4,     /* a CUDA call failed (message via rhseg_last_cuda_error) */
+    RHSEG_ETIMEOUT = -5,  /* a bounded device wait gave up                         */
+    RHSEG_ESTATE = -6,    /* call out of order (e.g. get_level before run)          */
+    RHSEG_ETRUNC = -7,    /* output buffer too small; the needed size is returned  */
+    RHSEG_EDEVICE = -8    /* no usable sm_103a device                              */
+};
+
+/* Parameters (Section 4.1; L, spectral clustering weight and the number of
+ * classes are the thesis's inputs). */
+typedef struct rhseg_params {
+    int32_t rnb_levels;    /* 1 <= L <= 6: the deepest level has 4^(L-1) sections   */
+    int32_t conv_nregions; /* final region count of the root HSEG (>= 1)            */
+    double  spclust_wght;  /* w in [0, 1]; 0 disables spectral merges (HSWO)        */
+    int32_t connectivity;  /* 4 or 8 (8 is the thesis's reassembly neighbourhood)   */
+    int32_t min_nregions;  /* per-section target below the root; 0 -> conv_nregions */
+    int32_t n_out_levels;  /* hierarchy snapshots kept at the root; 0 -> 1          */
+    int32_t seam_pass;     /* 1: boundary-artifact split pass at each reassembly    */
+    int32_t precision;     /* screen of the spectral step (results identical):
+                              0 = FP64 on CUDA cores,
+                              1 = FP16 region means on tcgen05 tensor cores, FP32 accumulate,
+                              2 = BF16 region means on tcgen05 tensor cores, FP32 accumulate,
+                              3 = FP32 on CUDA cores (the thesis kernel's arithmetic, Fig. 4.8) */
+    int32_t profile;       /* 1: time every step kernel with CUDA events (stats *_ms) */
+} rhseg_params;
+
+/* One merge-log record.  kind 0 = adjacent merge, 1 = spectral merge,
+ * 2 = seam split (survivor_id = region the pixel left, absorbed_id = the new
+ * one-pixel region's ID, key = K({p}, R), step = 0).  Canonical order:
+ * levels deepest first, sections in Z order, within a section the seam
+ * splits (raster order) then the HSEG merges in order; step counts HSEG
+ * iterations from 1. */
+typedef struct rhseg_merge {
+    int32_t level, section, step, kind;
+    int64_t survivor_id, absorbed_id;
+    double  key;            /* K = d^2, correctly rounded binary64           */
+    double  dissim;         /* sqrt(K), Eq. 1                                  */
+    int32_t nregions_after; /* section's region count after this record      */
+    int32_t pad;
+} rhseg_merge;
+
+typedef struct rhseg_stats {
+    int64_t pairs;            /* dissimilarities the method defines: adjacent pairs
+                                 of each adjacent step + non-adjacent pairs of each
+                                 spectral step                                    */
+    int64_t iterations;       /* HSEG iterations over all sections                */
+    int64_t merges_adj, merges_spec, seam_splits;
+    int64_t screened_pairs;   /* pairs the spectral screen evaluated              */
+    int64_t candidates;       /* pairs the screen passed to the exact re-check    */
+    int64_t fallbacks;        /* spectral steps resolved by exhaustive exact keys */
+    int32_t stalled_sections, n_levels_out;
+    double  run_ms;           /* device time of the last rhseg_run                */
+    int64_t kernel_launches;  /* kernels launched by the last rhseg_run            */
+    int64_t screen_launches;  /* spectral-screen launches                          */
+    double  screen_ms, adj_ms, spec_ms;  /* summed device time per step kernel
+                                            (profile = 1 only, else 0)            */
+    int32_t screen_impl;      /* 0 none, 1 FP64 CUDA cores, 2 FP32-accumulate CUDA
+                                 cores, 3 tcgen05 tensor cores                    */
+    int32_t pad;
+} rhseg_stats;
+
+typedef struct rhseg_handle rhseg_handle;
+
+/* Create from HOST buffers.  image: [rows][cols][bands] uint16 (copied);
+ * mask: [rows][cols], nonzero = no data, or NULL.  Device memory is
+ * allocated here (cudaMalloc) and owned by the handle.  The copy runs on
+ * `cuda_stream` (a cudaStream_t, NULL = legacy default stream). */
+int rhseg_create(const uint16_t *image, int32_t rows, int32_t cols, int32_t bands,
+                 const uint8_t *mask, const rhseg_params *p, void *cuda_stream,
+                 rhseg_handle **out);
+
+/* Create from DEVICE buffers that stay owned by the caller and must outlive
+ * the handle (same layouts as rhseg_create; read only). */
+int rhseg_create_device(const uint16_t *image_dev, int32_t rows, int32_t cols, int32_t bands,
+                        const uint8_t *mask_dev, const rhseg_params *p, void *cuda_stream,
+                        rhseg_handle **out);
+
+/* Replace the image (and mask) of a handle made by rhseg_create with new
+ * HOST buffers of the same shape; the copy runs on `cuda_stream` (NULL = the
+ * handle's stream) and is ordered before the next rhseg_run on that stream.
+ * The mask must be given iff the handle was created with one.  Pinned host
+ * memory makes the copy asynchronous; the buffers must stay valid until the
+ * next rhseg_run returns.  RHSEG_ESTATE for handles of rhseg_create_device;
+ * RHSEG_ERANGE if the new image breaks the exact-key bound. */
+int rhseg_set_image(rhseg_handle *h, const uint16_t *image, const uint8_t *mask, void *cuda_stream);
+
+/* Run the whole recursion on `cuda_stream` (NULL = the handle's stream) and
+ * wait for it.  May be called again; each call recomputes from the image. */
+int rhseg_run(rhseg_handle *h, void *cuda_stream);
+
+/* Number of hierarchy levels kept at the root (valid after run). */
+int rhseg_n_levels(const rhseg_handle *h, int32_t *n_levels);
+
+/* One hierarchy level, 0 = finest kept ... n_levels-1 = conv_nregions.
+ * labels: host [rows*cols] int32 (0 = masked, 1..R canonical) or NULL;
+ * band_sums: host [R*bands] int64 by canonical label or NULL;
+ * counts: host [R] int64 or NULL; nregions_out: R (may be NULL).
+ * Pass NULL outputs first to learn R. */
+int rhseg_get_level(rhseg_handle *h, int32_t level, int32_t *labels, int64_t *band_sums,
+                    int64_t *counts, int32_t *nregions_out);
+
+/* Full canonical merge log into host `log` (capacity log_cap records).
+ * *log_len receives the number of records; RHSEG_ETRUNC if log_cap is
+ * smaller (nothing written).  log may be NULL to query the length. */
+int rhseg_get_log(rhseg_handle *h, rhseg_merge *log, int64_t log_cap, int64_t *log_len);
+
+int rhseg_get_stats(const rhseg_handle *h, rhseg_stats *s);
+
+void rhseg_destroy(rhseg_handle *h);
+
+const char *rhseg_strerror(int code);
+const char *rhseg_last_cuda_error(void);
+
+/* Exact keys for explicit region pairs on the device: for t < npairs,
+ * out[t] = K(pair_i[t], pair_j[t]) from band sums S (int64 [nreg][bands],
+ * row stride `stride` elements) and counts n (int64 [nreg]).  All pointers
+ * are device pointers; runs on `cuda_stream` and does not wait. */
+int rhseg_keys(const int64_t *S, const int64_t *n, int32_t nreg, int32_t bands, int32_t stride,
+               const int32_t *pair_i, const int32_t *pair_j, int32_t npairs, double *out,
+               void *cuda_stream);
+
+/* Correctly rounded binary64 of N/D for 128-bit N, D given as (hi, lo)
+ * uint64 pairs, device pointers, n values (diagnostic of the key's final
+ * rounding).  Does not wait. */
+int rhseg_div_rn(const uint64_t *n_hi, const uint64_t *n_lo, const uint64_t *d_hi,
+                 const uint64_t *d_lo, int32_t n, double *out, void *cuda_stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RHSEG_H */

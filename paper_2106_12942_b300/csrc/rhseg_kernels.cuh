@@ -1,0 +1,1057 @@
+// rhseg_kernels.cuh -- level set-up, HSEG step and level-transition kernels.
+//
+// Data layout of a level (all sections of the level at once):
+//   slots      regions present at the level start, section-local index sorted
+//              by region ID (so slot order = ID order, reading R5);
+//   positions  compact list of live slots used by the spectral screen,
+//              rebuilt (stable) once an eighth of them died;
+//   adjacency  one dense bitmap per section, m0 x W words (W = ceil(m0/32)
+//              rounded to 4), symmetric, no self bits;
+//   bestK/P    per slot: the smallest (K, pair) over its adjacent partners
+//              (kept exact and current after every merge);
+//   log        one segment per (level, section).
+#pragma once
+#include "rhseg_dev.cuh"
+#include "../../include/rhseg.h"
+
+namespace rhseg {
+
+constexpr int STEP_THREADS = 512;
+constexpr int NB_CHUNK_WORDS = 64;      // adjacency words gathered per chunk
+constexpr int RESCAN_CAP = 512;
+
+struct PixGeom {
+    int32_t rows, cols, B, Bs;
+    const uint16_t *img;       // [P][B]
+    const uint8_t *mask;       // [P] or null
+};
+
+__device__ __forceinline__ bool unmasked(const PixGeom &g, int64_t p)
+{
+    return g.mask == nullptr || g.mask[p] == 0;
+}
+
+// section index (Z order) of pixel (y, x) at a level with `nbits` split
+// levels below the root: interleave row band and column band bits.
+__device__ __forceinline__ int32_t morton2(int32_t rb, int32_t cb, int nbits)
+{
+    int32_t s = 0;
+    for (int i = nbits - 1; i >= 0; i--) {
+        s = (s << 2) | (((rb >> i) & 1) << 1) | ((cb >> i) & 1);
+    }
+    return s;
+}
+
+// ---------------------------------------------------------------------------
+// Level set-up
+// ---------------------------------------------------------------------------
+
+// Deepest level: every unmasked pixel is a region with ID p+1 (reading R5).
+__global__ void k_init_labels(PixGeom g, uint32_t *label, uint8_t *isid, int32_t *srcslot)
+{
+    int64_t P = (int64_t)g.rows * g.cols;
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < P; p += (int64_t)gridDim.x * blockDim.x) {
+        bool u = unmasked(g, p);
+        label[p] = u ? (uint32_t)(p + 1) : 0u;
+        isid[p] = u ? 1 : 0;
+        srcslot[p] = -1;
+    }
+}
+
+// One block per section: raster scan of the section rectangle; every pixel
+// that carries a region ID (isid) gets the next slot.  Seam splits (kind 2
+// records) are written in the same raster order.
+__global__ void k_section_scan(PixGeom g, int32_t nsec, const int32_t *rect, const uint8_t *isid,
+                               const uint8_t *split, const double *split_key, const uint32_t *split_from,
+                               const int64_t *roff, int32_t *slot_of_id, SecState *st,
+                               rhseg_merge *log, const int64_t *loff, int32_t level)
+{
+    int sec = blockIdx.x;
+    if (sec >= nsec) return;
+    __shared__ int32_t wsum[32];
+    __shared__ int32_t wsplit[32];
+    __shared__ int32_t base, sbase;
+    int r0 = rect[4 * sec], r1 = rect[4 * sec + 1], c0 = rect[4 * sec + 2], c1 = rect[4 * sec + 3];
+    int64_t w = c1 - c0;
+    int64_t area = (int64_t)(r1 - r0) * w;
+    if (threadIdx.x == 0) { base = 0; sbase = 0; }
+    __syncthreads();
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int64_t c = 0; c < area; c += blockDim.x) {
+        int64_t li = c + threadIdx.x;
+        int flag = 0, sp = 0;
+        int64_t p = 0;
+        if (li < area) {
+            p = (int64_t)(r0 + li / w) * g.cols + (c0 + li % w);
+            flag = isid[p];
+            sp = split ? split[p] : 0;
+        }
+        unsigned bal = __ballot_sync(0xffffffffu, flag);
+        unsigned bsp = __ballot_sync(0xffffffffu, sp);
+        int pre = __popc(bal & ((1u << lane) - 1));
+        int spre = __popc(bsp & ((1u << lane) - 1));
+        if (lane == 0) { wsum[wid] = __popc(bal); wsplit[wid] = __popc(bsp); }
+        __syncthreads();
+        int off = 0, soff = 0, tot = 0, stot = 0;
+        for (int i = 0; i < nw; i++) {
+            if (i < wid) { off += wsum[i]; soff += wsplit[i]; }
+            tot += wsum[i]; stot += wsplit[i];
+        }
+        if (flag) slot_of_id[p] = (int32_t)(roff[sec] + base + off + pre);
+        if (sp) {
+            int64_t k = sbase + soff + spre;
+            rhseg_merge m;
+            m.level = level; m.section = sec; m.step = 0; m.kind = 2;
+            m.survivor_id = split_from[p]; m.absorbed_id = p + 1;
+            m.key = split_key[p]; m.dissim = sqrt(split_key[p]);
+            m.nregions_after = 0; m.pad = 0;      // patched once m0 is known
+            log[loff[sec] + k] = m;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) { base += tot; sbase += stot; }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        SecState s = {};
+        s.m0 = base;
+        s.count = base;
+        s.log_n = sbase;
+        s.nsplit = sbase;
+        st[sec] = s;
+    }
+}
+
+// Fill the slot tables from the region sources (warp per region).
+// srcslot[id-1] = previous-level slot of the region with that ID, or -1 for
+// a one-pixel region taken from the image.
+__global__ void k_fill_tables(PixGeom g, int64_t P, const uint8_t *isid, const int32_t *srcslot,
+                              const int32_t *slot_of_id, const int64_t *S_prev, const int64_t *n_prev,
+                              int64_t *S, int64_t *n, uint32_t *rid, uint8_t *alive, int32_t *parent,
+                              int32_t *absorbed_at, uint64_t *bestK, int32_t *bestP)
+{
+    int lane = threadIdx.x & 31;
+    int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t p = warp; p < P; p += nwarps) {
+        if (!isid[p]) continue;
+        int64_t gsl = slot_of_id[p];
+        int32_t src = srcslot[p];
+        int64_t *dst = S + gsl * g.Bs;
+        if (src < 0) {
+            const uint16_t *x = g.img + p * g.B;
+            for (int b = lane; b < g.Bs; b += 32) dst[b] = (b < g.B) ? (int64_t)x[b] : 0;
+        } else {
+            const int64_t *s = S_prev + (int64_t)src * g.Bs;
+            for (int b = lane; b < g.Bs; b += 32) dst[b] = s[b];
+        }
+        if (lane == 0) {
+            n[gsl] = (src < 0) ? 1 : n_prev[src];
+            rid[gsl] = (uint32_t)(p + 1);
+            alive[gsl] = 1;
+            absorbed_at[gsl] = 0x7fffffff;
+            bestK[gsl] = RHSEG_KEY_NONE;
+            bestP[gsl] = -1;
+        }
+    }
+}
+
+// parent[g] = g for all slots of the level (global slot indices)
+__global__ void k_init_parent(int32_t *parent, const int64_t *roff, const SecState *st, int32_t nsec)
+{
+    int sec = blockIdx.y;
+    if (sec >= nsec) return;
+    int m0 = st[sec].m0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m0; i += gridDim.x * blockDim.x)
+        parent[roff[sec] + i] = (int32_t)(roff[sec] + i);
+}
+
+// Adjacency bitmap from the label map: pixels p, q neighbours (4 or 8
+// connectivity) inside the same section, both unmasked, different labels.
+__global__ void k_build_adj(PixGeom g, const uint32_t *label, const int32_t *slot_of_id,
+                            const int32_t *rowband, const int32_t *colband, int nbits, int conn,
+                            const int64_t *roff, const int64_t *aoff, const int32_t *Wrow, uint32_t *adj)
+{
+    int64_t P = (int64_t)g.rows * g.cols;
+    // forward half of the neighbourhood: each undirected pixel pair once
+    const int dy8[4] = {0, 1, 1, 1}, dx8[4] = {1, -1, 0, 1};
+    const int dy4[2] = {0, 1}, dx4[2] = {1, 0};
+    int nn = conn == 8 ? 4 : 2;
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < P; p += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t lp = label[p];
+        if (lp == 0) continue;
+        int y = (int)(p / g.cols), x = (int)(p % g.cols);
+        int sp = morton2(rowband[y], colband[x], nbits);
+        for (int k = 0; k < nn; k++) {
+            int yy = y + (conn == 8 ? dy8[k] : dy4[k]);
+            int xx = x + (conn == 8 ? dx8[k] : dx4[k]);
+            if (yy < 0 || yy >= g.rows || xx < 0 || xx >= g.cols) continue;
+            int64_t q = (int64_t)yy * g.cols + xx;
+            uint32_t lq = label[q];
+            if (lq == 0 || lq == lp) continue;
+            if (morton2(rowband[yy], colband[xx], nbits) != sp) continue;
+            int64_t a = slot_of_id[lp - 1] - roff[sp];
+            int64_t b = slot_of_id[lq - 1] - roff[sp];
+            int W = Wrow[sp];
+            uint32_t *ra = adj + aoff[sp] + a * W;
+            uint32_t *rb = adj + aoff[sp] + b * W;
+            uint32_t ma = 1u << (b & 31), mb = 1u << (a & 31);
+            if (!(ra[b >> 5] & ma)) atomicOr(&ra[b >> 5], ma);
+            if (!(rb[a >> 5] & mb)) atomicOr(&rb[a >> 5], mb);
+        }
+    }
+}
+
+// Exact best adjacent partner of every slot (warp per slot).
+__global__ void k_init_best(LevelDev L)
+{
+    int sec = blockIdx.y;
+    const SecState &s = L.st[sec];
+    int m0 = s.m0;
+    int W = L.W[sec];
+    int64_t ro = L.roff[sec];
+    const uint32_t *A = L.adj + L.aoff[sec];
+    int lane = threadIdx.x & 31;
+    int wpb = blockDim.x >> 5;
+    for (int i = blockIdx.x * wpb + (threadIdx.x >> 5); i < m0; i += gridDim.x * wpb) {
+        const uint32_t *row = A + (int64_t)i * W;
+        PairKey best = pk_none();
+        const int64_t *Si = L.S + (ro + i) * L.Bs;
+        int64_t ni = L.n[ro + i];
+        for (int w = 0; w < W; w++) {
+            uint32_t bits = row[w];
+            while (bits) {
+                int r = w * 32 + __ffs(bits) - 1;
+                bits &= bits - 1;
+                double K = warp_key(Si, ni, L.S + (ro + r) * L.Bs, L.n[ro + r], L.B, L.err);
+                PairKey c = pk_make(dbits(K), i, r);
+                if (pk_less(c, best)) best = c;
+            }
+        }
+        if (lane == 0) {
+            L.bestK[ro + i] = best.k;
+            L.bestP[ro + i] = (best.k == RHSEG_KEY_NONE) ? -1 : (int32_t)(best.lo == (uint32_t)i ? best.hi : best.lo);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Screen operand rows (region means relative to a per-section reference).
+// ---------------------------------------------------------------------------
+
+struct ScreenConst {
+    double u, eta;        // componentwise rounding of the operand: |e| <= u|x| + eta
+    double two_one_inv_delta;   // 2 (1 + 1/delta)
+    double gamma;         // accumulation + evaluation slack, relative to q
+    double kscale;        // (1 + delta) * 4^-sigma
+    double xscale;        // 2^-sigma
+};
+
+template <typename T>
+__device__ __forceinline__ T to_op(double v);
+template <> __device__ __forceinline__ double to_op<double>(double v) { return v; }
+template <> __device__ __forceinline__ float to_op<float>(double v) { return __double2float_rn(v); }
+template <> __device__ __forceinline__ __half to_op<__half>(double v) { return __double2half(v); }
+template <> __device__ __forceinline__ __nv_bfloat16 to_op<__nv_bfloat16>(double v) { return __double2bfloat16(v); }
+
+template <typename T>
+__device__ __forceinline__ double op_to_d(T v);
+template <> __device__ __forceinline__ double op_to_d<double>(double v) { return v; }
+template <> __device__ __forceinline__ double op_to_d<float>(float v) { return (double)v; }
+template <> __device__ __forceinline__ double op_to_d<__half>(__half v) { return (double)__half2float(v); }
+template <> __device__ __forceinline__ double op_to_d<__nv_bfloat16>(__nv_bfloat16 v) { return (double)__bfloat162float(v); }
+
+// Write operand row `pos` from slot `slot` (warp-cooperative); returns q.
+template <typename T>
+__device__ void warp_write_row(const LevelDev &L, int sec, int slot, int pos, const ScreenConst &sc)
+{
+    int lane = threadIdx.x & 31;
+    int64_t ro = L.roff[sec];
+    const int64_t *S = L.S + (ro + slot) * L.Bs;
+    int64_t n = L.n[ro + slot];
+    const int32_t *ref = L.ref + (int64_t)sec * L.Bs;
+    T *X = (T *)L.X + (L.poff[sec] + pos) * (int64_t)L.Bpad;
+    double rinv = 1.0 / (double)n;
+    double q = 0.0;
+    for (int b = lane; b < L.Bpad; b += 32) {
+        T v;
+        if (b < L.B) {
+            double x = (double)(S[b] - n * (int64_t)ref[b]) * rinv * sc.xscale;
+            v = to_op<T>(x);
+        } else {
+            v = to_op<T>(0.0);
+        }
+        X[b] = v;
+        double xd = op_to_d<T>(v);
+        q = fma(xd, xd, q);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) q += __shfl_xor_sync(0xffffffffu, q, o);
+    if (lane == 0) {
+        double qq = q * (1.0 + 0x1p-40);
+        double eps = (sc.u * sqrt(qq) + sc.eta * sqrt((double)L.B)) * (1.0 + 0x1p-30);
+        double A = qq - sc.two_one_inv_delta * eps * eps - sc.gamma * qq;
+        double k = sc.kscale / (double)n * (1.0 + 0x1p-40);
+        if (L.precision == 0) { L.Ad[L.poff[sec] + pos] = A; L.kd[L.poff[sec] + pos] = k; }
+        else { L.Af[L.poff[sec] + pos] = __double2float_rd(A); L.kf[L.poff[sec] + pos] = __double2float_ru(k); }
+    }
+}
+
+__device__ __forceinline__ void mark_pos_dead(const LevelDev &L, int sec, int pos)
+{
+    if (L.precision == 0) L.Ad[L.poff[sec] + pos] = __longlong_as_double(0x7FF0000000000000ll);
+    else L.Af[L.poff[sec] + pos] = __int_as_float(0x7f800000);
+}
+
+template <typename T>
+__device__ void block_write_rows(const LevelDev &L, int sec, int mc_new, int pos_end, const ScreenConst &sc)
+{
+    int wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int pos = wid; pos < mc_new; pos += nw) warp_write_row<T>(L, sec, L.slot_of_pos[L.poff[sec] + pos], pos, sc);
+    for (int pos = mc_new + threadIdx.x; pos < pos_end; pos += blockDim.x) mark_pos_dead(L, sec, pos);
+}
+
+__device__ __forceinline__ void write_row_any(const LevelDev &L, int sec, int slot, int pos, const ScreenConst &sc)
+{
+    switch (L.precision) {
+    case 0: warp_write_row<double>(L, sec, slot, pos, sc); break;
+    case 1: warp_write_row<__half>(L, sec, slot, pos, sc); break;
+    case 2: warp_write_row<__nv_bfloat16>(L, sec, slot, pos, sc); break;
+    default: warp_write_row<float>(L, sec, slot, pos, sc); break;
+    }
+}
+
+__device__ __forceinline__ void block_write_rows_any(const LevelDev &L, int sec, int mc_new, int pos_end, const ScreenConst &sc)
+{
+    switch (L.precision) {
+    case 0: block_write_rows<double>(L, sec, mc_new, pos_end, sc); break;
+    case 1: block_write_rows<__half>(L, sec, mc_new, pos_end, sc); break;
+    case 2: block_write_rows<__nv_bfloat16>(L, sec, mc_new, pos_end, sc); break;
+    default: block_write_rows<float>(L, sec, mc_new, pos_end, sc); break;
+    }
+}
+
+// Per section: reference spectrum, positions, screen rows, counters.
+__global__ void __launch_bounds__(STEP_THREADS) k_init_section(LevelDev L, ScreenConst sc, int32_t target)
+{
+    int sec = blockIdx.x;
+    if (sec >= L.nsec) return;
+    __shared__ long long red[32];
+    SecState *st = &L.st[sec];
+    int m0 = st->m0;
+    int64_t ro = L.roff[sec];
+    // reference spectrum: floor of the section's mean pixel spectrum
+    long long ntot = 0;
+    for (int i = threadIdx.x; i < m0; i += blockDim.x) ntot += L.n[ro + i];
+    ntot = block_sum_ll(ntot, red);
+    int32_t *ref = (int32_t *)(L.ref + (int64_t)sec * L.Bs);
+    for (int b = threadIdx.x; b < L.Bs; b += blockDim.x) {
+        long long v = 0;
+        if (b < L.B)
+            for (int i = 0; i < m0; i++) v += L.S[(ro + i) * L.Bs + b];
+        ref[b] = (b < L.B && ntot > 0) ? (int32_t)(v / ntot) : 0;
+    }
+    __syncthreads();
+    __threadfence_block();
+    for (int i = threadIdx.x; i < m0; i += blockDim.x) {
+        L.pos_of_slot[ro + i] = i;
+        L.slot_of_pos[L.poff[sec] + i] = i;
+    }
+    // adjacent pairs
+    const uint32_t *A = L.adj + L.aoff[sec];
+    int W = L.W[sec];
+    long long pc = 0;
+    for (int64_t w = threadIdx.x; w < (int64_t)m0 * W; w += blockDim.x) pc += __popc(A[w]);
+    pc = block_sum_ll(pc, red);
+    __syncthreads();
+    int pend = ((m0 + 127) / 128) * 128;
+    block_write_rows_any(L, sec, m0, pend, sc);
+    if (threadIdx.x == 0) {
+        st->target = target;
+        st->nadj = pc / 2;
+        st->mc = m0;
+        st->done = (m0 <= target) ? 1 : 0;
+        st->Kadj = __longlong_as_double(0x7FF0000000000000ll);
+        st->tthr = st->Kadj;
+        // seam records carry the count after the pass
+        rhseg_merge *lg = (rhseg_merge *)L.log + L.loff[sec];
+        for (int64_t k = 0; k < st->log_n; k++) lg[k].nregions_after = m0;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// HSEG step kernels
+// ---------------------------------------------------------------------------
+
+struct StepSmem {
+    PairKey pk[32];
+    long long ll[32];
+    int32_t nb[NB_CHUNK_WORDS * 32];
+    int32_t nnb;
+    int32_t rescan[RESCAN_CAP];
+    int32_t nrescan;
+    int32_t rescan_overflow;
+};
+
+// Min over adjacent partners of slot r (exact keys), whole block.
+__device__ PairKey block_row_best(const LevelDev &L, int sec, int r, StepSmem &sm)
+{
+    int64_t ro = L.roff[sec];
+    int W = L.W[sec];
+    const uint32_t *row = L.adj + L.aoff[sec] + (int64_t)r * W;
+    const int64_t *Sr = L.S + (ro + r) * L.Bs;
+    int64_t nr = L.n[ro + r];
+    int wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    PairKey best = pk_none();
+    for (int w0 = 0; w0 < W; w0 += NB_CHUNK_WORDS) {
+        __syncthreads();
+        if (threadIdx.x == 0) sm.nnb = 0;
+        __syncthreads();
+        for (int w = w0 + threadIdx.x; w < min(W, w0 + NB_CHUNK_WORDS); w += blockDim.x) {
+            uint32_t bits = row[w];
+            while (bits) {
+                int q = w * 32 + __ffs(bits) - 1;
+                bits &= bits - 1;
+                sm.nb[atomicAdd(&sm.nnb, 1)] = q;
+            }
+        }
+        __syncthreads();
+        int cnt = sm.nnb;
+        for (int t = wid; t < cnt; t += nw) {
+            int q = sm.nb[t];
+            double K = warp_key(Sr, nr, L.S + (ro + q) * L.Bs, L.n[ro + q], L.B, L.err);
+            PairKey c = pk_make(dbits(K), r, q);
+            if (pk_less(c, best)) best = c;
+        }
+    }
+    return block_min_pk(best, sm.pk);
+}
+
+// Merge slot b into slot a (a < b, so a keeps the smaller ID).  Whole block.
+__device__ void block_merge(const LevelDev &L, int sec, int a, int b, double K, int kind,
+                            const ScreenConst &sc, StepSmem &sm)
+{
+    SecState *st = &L.st[sec];
+    int64_t ro = L.roff[sec];
+    int W = L.W[sec];
+    uint32_t *A = L.adj + L.aoff[sec];
+    uint32_t *rowA = A + (int64_t)a * W;
+    uint32_t *rowB = A + (int64_t)b * W;
+    int tid = threadIdx.x, nt = blockDim.x;
+    int ab = (rowA[b >> 5] >> (b & 31)) & 1;
+    long long pa = 0, pb = 0;
+    for (int w = tid; w < W; w += nt) { pa += __popc(rowA[w]); pb += __popc(rowB[w]); }
+    pa = block_sum_ll(pa, sm.ll);
+    pb = block_sum_ll(pb, sm.ll);
+    __syncthreads();
+    // features (exact integers)
+    for (int k = tid; k < L.Bs; k += nt) L.S[(ro + a) * L.Bs + k] += L.S[(ro + b) * L.Bs + k];
+    if (tid == 0) {
+        L.n[ro + a] += L.n[ro + b];
+        L.alive[ro + b] = 0;
+        L.parent[ro + b] = (int32_t)(ro + a);
+        int ord = ++st->nmerge;
+        if (kind == 0) st->madj += 1; else st->mspec += 1;
+        L.absorbed_at[ro + b] = ord;
+        L.bestK[ro + b] = RHSEG_KEY_NONE;
+        L.bestP[ro + b] = -1;
+        st->count -= 1;
+        rhseg_merge m;
+        m.level = L.level; m.section = sec; m.step = st->iter; m.kind = kind;
+        m.survivor_id = L.rid[ro + a]; m.absorbed_id = L.rid[ro + b];
+        m.key = K; m.dissim = sqrt(K);
+        m.nregions_after = st->count; m.pad = 0;
+        ((rhseg_merge *)L.log)[L.loff[sec] + st->log_n] = m;
+        st->log_n += 1;
+    }
+    // adjacency: row a |= row b, neighbours of b now point to a
+    for (int w = tid; w < W; w += nt) rowA[w] |= rowB[w];
+    __syncthreads();
+    if (tid == 0) {
+        rowA[a >> 5] &= ~(1u << (a & 31));
+        rowA[b >> 5] &= ~(1u << (b & 31));
+    }
+    for (int w = tid; w < W; w += nt) {
+        uint32_t bits = rowB[w];
+        while (bits) {
+            int r = w * 32 + __ffs(bits) - 1;
+            bits &= bits - 1;
+            if (r == a) continue;
+            uint32_t *rowR = A + (int64_t)r * W;
+            atomicOr(&rowR[a >> 5], 1u << (a & 31));
+            atomicAnd(&rowR[b >> 5], ~(1u << (b & 31)));
+        }
+    }
+    __syncthreads();
+    for (int w = tid; w < W; w += nt) rowB[w] = 0;
+    __syncthreads();
+    long long pn = 0;
+    for (int w = tid; w < W; w += nt) pn += __popc(rowA[w]);
+    pn = block_sum_ll(pn, sm.ll);
+    if (tid == 0) {
+        st->nadj = st->nadj - pa - pb + ab + pn;
+        sm.nrescan = 0;
+        sm.rescan_overflow = 0;
+    }
+    __syncthreads();
+    // exact best partners: row a in full, neighbours of a incrementally
+    const int64_t *Sa = L.S + (ro + a) * L.Bs;
+    int64_t na = L.n[ro + a];
+    int wid = tid >> 5, nw = nt >> 5, lane = tid & 31;
+    PairKey best = pk_none();
+    for (int w0 = 0; w0 < W; w0 += NB_CHUNK_WORDS) {
+        __syncthreads();
+        if (tid == 0) sm.nnb = 0;
+        __syncthreads();
+        for (int w = w0 + tid; w < min(W, w0 + NB_CHUNK_WORDS); w += nt) {
+            uint32_t bits = rowA[w];
+            while (bits) {
+                int q = w * 32 + __ffs(bits) - 1;
+                bits &= bits - 1;
+                sm.nb[atomicAdd(&sm.nnb, 1)] = q;
+            }
+        }
+        __syncthreads();
+        int cnt = sm.nnb;
+        for (int t = wid; t < cnt; t += nw) {
+            int r = sm.nb[t];
+            double Kr = warp_key(Sa, na, L.S + (ro + r) * L.Bs, L.n[ro + r], L.B, L.err);
+            PairKey c = pk_make(dbits(Kr), a, r);
+            if (pk_less(c, best)) best = c;
+            if (lane == 0) {
+                int bp = L.bestP[ro + r];
+                if (bp == a || bp == b || bp < 0) {
+                    int k = atomicAdd(&sm.nrescan, 1);
+                    if (k < RESCAN_CAP) sm.rescan[k] = r; else sm.rescan_overflow = 1;
+                } else {
+                    PairKey old = pk_make(L.bestK[ro + r], r, bp);
+                    PairKey nc = pk_make(dbits(Kr), r, a);
+                    if (pk_less(nc, old)) { L.bestK[ro + r] = nc.k; L.bestP[ro + r] = a; }
+                }
+            }
+        }
+    }
+    best = block_min_pk(best, sm.pk);
+    if (tid == 0) {
+        L.bestK[ro + a] = best.k;
+        L.bestP[ro + a] = (best.k == RHSEG_KEY_NONE) ? -1 : (int32_t)(best.lo == (uint32_t)a ? best.hi : best.lo);
+    }
+    __syncthreads();
+    int nres = min(sm.nrescan, RESCAN_CAP);
+    int ovf = sm.rescan_overflow;
+    if (!ovf) {
+        for (int k = 0; k < nres; k++) {
+            int r = sm.rescan[k];
+            PairKey rb = block_row_best(L, sec, r, sm);
+            if (tid == 0) {
+                L.bestK[ro + r] = rb.k;
+                L.bestP[ro + r] = (rb.k == RHSEG_KEY_NONE) ? -1 : (int32_t)(rb.lo == (uint32_t)r ? rb.hi : rb.lo);
+            }
+            __syncthreads();
+        }
+    } else {
+        // too many rows to re-scan one by one: re-scan every neighbour of a
+        for (int w = 0; w < W; w++) {
+            uint32_t bits = rowA[w];
+            while (bits) {
+                int r = w * 32 + __ffs(bits) - 1;
+                bits &= bits - 1;
+                PairKey rb = block_row_best(L, sec, r, sm);
+                if (tid == 0) {
+                    L.bestK[ro + r] = rb.k;
+                    L.bestP[ro + r] = (rb.k == RHSEG_KEY_NONE) ? -1 : (int32_t)(rb.lo == (uint32_t)r ? rb.hi : rb.lo);
+                }
+                __syncthreads();
+            }
+        }
+    }
+    // screen rows of a (new features) and b (dead)
+    int pa_pos = L.pos_of_slot[ro + a], pb_pos = L.pos_of_slot[ro + b];
+    if (wid == 0) write_row_any(L, sec, a, pa_pos, sc);
+    if (tid == 32) mark_pos_dead(L, sec, pb_pos);
+    __syncthreads();
+}
+
+// Stable compaction of the screen positions to the live slots.
+__device__ void block_compact(const LevelDev &L, int sec, const ScreenConst &sc, StepSmem &sm)
+{
+    SecState *st = &L.st[sec];
+    int m0 = st->m0;
+    int64_t ro = L.roff[sec];
+    int old_mc = st->mc;
+    __shared__ int32_t wcnt[32];
+    __shared__ int32_t base;
+    if (threadIdx.x == 0) base = 0;
+    __syncthreads();
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int c = 0; c < m0; c += blockDim.x) {
+        int i = c + threadIdx.x;
+        int f = (i < m0) ? L.alive[ro + i] : 0;
+        unsigned bal = __ballot_sync(0xffffffffu, f);
+        if (lane == 0) wcnt[wid] = __popc(bal);
+        __syncthreads();
+        int off = 0, tot = 0;
+        for (int k = 0; k < nw; k++) { if (k < wid) off += wcnt[k]; tot += wcnt[k]; }
+        if (f) {
+            int pos = base + off + __popc(bal & ((1u << lane) - 1));
+            L.pos_of_slot[ro + i] = pos;
+            L.slot_of_pos[L.poff[sec] + pos] = i;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) base += tot;
+        __syncthreads();
+    }
+    int mc = base;
+    int pend = ((old_mc + 127) / 128) * 128;
+    block_write_rows_any(L, sec, mc, pend, sc);
+    __syncthreads();
+    if (threadIdx.x == 0) st->mc = mc;
+    __syncthreads();
+}
+
+// Step 2 of HSEG: merge the adjacent pair of minimum key.
+__global__ void __launch_bounds__(STEP_THREADS) k_adj_step(LevelDev L, ScreenConst sc)
+{
+    int sec = blockIdx.x;
+    if (sec >= L.nsec) return;
+    __shared__ StepSmem sm;
+    SecState *st = &L.st[sec];
+    if (st->done) return;
+    __syncthreads();
+    if (st->count <= st->target) {
+        if (threadIdx.x == 0) { st->done = 1; st->spec_pending = 0; }
+        return;
+    }
+    int64_t ro = L.roff[sec];
+    int m0 = st->m0;
+    if (threadIdx.x == 0) { st->iter += 1; st->pairs += st->nadj; }
+    PairKey best = pk_none();
+    for (int i = threadIdx.x; i < m0; i += blockDim.x) {
+        if (!L.alive[ro + i]) continue;
+        uint64_t k = L.bestK[ro + i];
+        if (k == RHSEG_KEY_NONE) continue;
+        PairKey c = pk_make(k, i, L.bestP[ro + i]);
+        if (pk_less(c, best)) best = c;
+    }
+    best = block_min_pk(best, sm.pk);
+    __syncthreads();
+    int merged = 0;
+    double Kadj = __longlong_as_double(0x7FF0000000000000ll);
+    if (best.k != RHSEG_KEY_NONE) {
+        Kadj = __longlong_as_double((long long)best.k);
+        block_merge(L, sec, (int)best.lo, (int)best.hi, Kadj, 0, sc, sm);
+        merged = 1;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        st->merged_adj = merged;
+        st->Kadj = Kadj;
+        if (merged && st->count <= st->target) {
+            st->done = 1;
+            st->spec_pending = 0;
+        } else if (L.w > 0.0) {
+            st->spec_pending = 1;
+            st->tthr = merged ? L.ww * Kadj : Kadj;
+            st->ncand = 0;
+        } else {
+            st->spec_pending = 0;
+            if (!merged) { st->stalled = 1; st->done = 1; }
+        }
+    }
+}
+
+// Step 3 of HSEG: exact re-check of the screen's candidates (or of every
+// non-adjacent pair when no finite threshold exists or the candidate buffer
+// overflowed), merge of the minimum if below the threshold.
+__global__ void __launch_bounds__(STEP_THREADS) k_spec_step(LevelDev L, ScreenConst sc)
+{
+    int sec = blockIdx.x;
+    if (sec >= L.nsec) return;
+    __shared__ StepSmem sm;
+    SecState *st = &L.st[sec];
+    if (!st->spec_pending) return;
+    __syncthreads();
+    int64_t ro = L.roff[sec];
+    int m0 = st->m0;
+    int W = L.W[sec];
+    const uint32_t *A = L.adj + L.aoff[sec];
+    double t = st->tthr;
+    int count = st->count;
+    int mc = st->mc;
+    uint32_t ncand = st->ncand;
+    bool finite = t < __longlong_as_double(0x7FF0000000000000ll);
+    bool exhaustive = !finite || (int64_t)ncand > L.cand_cap;
+    int wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    PairKey best = pk_none();
+    if (!exhaustive) {
+        const uint32_t *cand = L.cand + (int64_t)sec * L.cand_cap * 2;
+        const int32_t *sop = L.slot_of_pos + L.poff[sec];
+        for (uint32_t c = wid; c < ncand; c += nw) {
+            int i = sop[cand[2 * c]], j = sop[cand[2 * c + 1]];
+            if (i == j || !L.alive[ro + i] || !L.alive[ro + j]) continue;
+            if ((A[(int64_t)i * W + (j >> 5)] >> (j & 31)) & 1) continue;
+            double K = warp_key(L.S + (ro + i) * L.Bs, L.n[ro + i], L.S + (ro + j) * L.Bs, L.n[ro + j], L.B, L.err);
+            if (!(K < t)) continue;
+            PairKey pc = pk_make(dbits(K), i, j);
+            if (pk_less(pc, best)) best = pc;
+        }
+    } else {
+        // every unordered pair of live, non-adjacent slots
+        int64_t npair = (int64_t)m0 * (m0 - 1) / 2;
+        for (int64_t e = wid; e < npair; e += nw) {
+            // decode e -> (i, j), i < j, row-major upper triangle
+            int64_t i = (int64_t)((2.0 * m0 - 1 - sqrt((2.0 * m0 - 1) * (2.0 * m0 - 1) - 8.0 * e)) / 2);
+            while (i > 0 && i * (2 * m0 - i - 1) / 2 > e) i--;
+            while ((i + 1) * (2 * m0 - i - 2) / 2 <= e) i++;
+            int64_t j = e - i * (2 * m0 - i - 1) / 2 + i + 1;
+            if (!L.alive[ro + i] || !L.alive[ro + j]) continue;
+            if ((A[i * W + (j >> 5)] >> (j & 31)) & 1) continue;
+            double K = warp_key(L.S + (ro + i) * L.Bs, L.n[ro + i], L.S + (ro + j) * L.Bs, L.n[ro + j], L.B, L.err);
+            if (!(K < t)) continue;
+            PairKey pc = pk_make(dbits(K), (int)i, (int)j);
+            if (pk_less(pc, best)) best = pc;
+        }
+    }
+    best = block_min_pk(best, sm.pk);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        st->pairs += (int64_t)count * (count - 1) / 2 - st->nadj;
+        st->cands += exhaustive ? 0 : (int64_t)ncand;
+        st->fallbacks += exhaustive ? 1 : 0;
+        if (!exhaustive) st->screened += (int64_t)mc * (mc - 1) / 2;
+    }
+    int merged = 0;
+    if (best.k != RHSEG_KEY_NONE) {
+        block_merge(L, sec, (int)best.lo, (int)best.hi, __longlong_as_double((long long)best.k), 1, sc, sm);
+        merged = 1;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        st->spec_pending = 0;
+        st->ncand = 0;
+        if (!merged && !st->merged_adj) { st->stalled = 1; st->done = 1; }
+        if (st->count <= st->target) st->done = 1;
+    }
+    __syncthreads();
+    if (!st->done && st->count <= (st->mc * 7) / 8 && st->mc > 128) block_compact(L, sec, sc, sm);
+}
+
+// ---------------------------------------------------------------------------
+// Level transitions
+// ---------------------------------------------------------------------------
+
+// Resolve each slot's root in the merge forest (pointer jumping in place;
+// parent pointers are global slot indices).
+__global__ void k_resolve_roots(int32_t *parent, const int64_t *roff, const SecState *st, int32_t nsec)
+{
+    int sec = blockIdx.x;
+    if (sec >= nsec) return;
+    int m0 = st[sec].m0;
+    int64_t ro = roff[sec];
+    __shared__ int changed;
+    for (int it = 0; it < 40; it++) {
+        __syncthreads();
+        if (threadIdx.x == 0) changed = 0;
+        __syncthreads();
+        for (int i = threadIdx.x; i < m0; i += blockDim.x) {
+            int p = parent[ro + i];
+            int pp = parent[p];
+            if (pp != p) { parent[ro + i] = pp; changed = 1; }
+        }
+        __syncthreads();
+        if (!changed) break;
+    }
+}
+
+// Pixel labels after a level: the ID of the root of the pixel's region.
+__global__ void k_relabel(int64_t P, uint32_t *label, const int32_t *slot_of_id, const int32_t *parent,
+                          const uint32_t *rid)
+{
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < P; p += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t l = label[p];
+        if (!l) continue;
+        label[p] = rid[parent[slot_of_id[l - 1]]];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Seam pass (boundary-artifact removal, Section 6.2 future work; reading R7)
+// ---------------------------------------------------------------------------
+
+struct SeamGeom {
+    const int32_t *rb_c, *cb_c;   // row / column band at the child level
+    int nbits_p;                  // split bits of the parent level
+    int conn;
+};
+
+__device__ __forceinline__ void parent_and_quad(const SeamGeom &sg, int y, int x, int32_t &par, int &quad)
+{
+    int rb = sg.rb_c[y], cb = sg.cb_c[x];
+    par = morton2(rb >> 1, cb >> 1, sg.nbits_p);
+    quad = ((rb & 1) << 1) | (cb & 1);
+}
+
+__device__ __forceinline__ int nb_dy(int conn, int k)
+{
+    const int d8[8] = {-1, -1, -1, 0, 0, 1, 1, 1};
+    const int d4[4] = {-1, 0, 0, 1};
+    return conn == 8 ? d8[k] : d4[k];
+}
+__device__ __forceinline__ int nb_dx(int conn, int k)
+{
+    const int d8[8] = {-1, 0, 1, -1, 1, -1, 0, 1};
+    const int d4[4] = {0, -1, 1, 0};
+    return conn == 8 ? d8[k] : d4[k];
+}
+
+// Seam pixels: unmasked, with a neighbour in the same parent section but in
+// another child quadrant.
+__global__ void k_seam_detect(PixGeom g, SeamGeom sg, const uint32_t *label, int32_t *seam_list,
+                              int32_t *nseam, int32_t seam_cap)
+{
+    int64_t P = (int64_t)g.rows * g.cols;
+    int nn = sg.conn == 8 ? 8 : 4;
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < P; p += (int64_t)gridDim.x * blockDim.x) {
+        if (!label[p]) continue;
+        int y = (int)(p / g.cols), x = (int)(p % g.cols);
+        int32_t par; int qd;
+        parent_and_quad(sg, y, x, par, qd);
+        bool seam = false;
+        for (int k = 0; k < nn && !seam; k++) {
+            int yy = y + nb_dy(sg.conn, k), xx = x + nb_dx(sg.conn, k);
+            if (yy < 0 || yy >= g.rows || xx < 0 || xx >= g.cols) continue;
+            int64_t q = (int64_t)yy * g.cols + xx;
+            if (!label[q]) continue;
+            int32_t par2; int qd2;
+            parent_and_quad(sg, yy, xx, par2, qd2);
+            if (par2 == par && qd2 != qd) seam = true;
+        }
+        if (seam) {
+            int k = atomicAdd(nseam, 1);
+            if (k < seam_cap) seam_list[k] = (int32_t)p;
+        }
+    }
+}
+
+// K({p}, region) for a one-pixel region p (warp-cooperative, exact).
+__device__ __forceinline__ double warp_key_pixel(const uint16_t *xp, const int64_t *Sj, int64_t nj, int B,
+                                                 int32_t *err)
+{
+    int lane = threadIdx.x & 31;
+    u128 acc = {0, 0};
+    for (int b = lane; b < B; b += 32) {
+        int64_t d = nj * (int64_t)xp[b] - Sj[b];
+        uint64_t a = (uint64_t)(d < 0 ? -d : d);
+        acc = u128_add(acc, u128_sq(a));
+    }
+    acc = warp_sum_u128(acc);
+    double K = 0.0;
+    if (lane == 0) {
+        u128 D = u128_mul64((uint64_t)nj, (uint64_t)(nj + 1));
+        K = div_rn_u128(acc, D, err);
+    }
+    return __shfl_sync(0xffffffffu, K, 0);
+}
+
+// Split decisions against the pre-pass state (warp per seam pixel).
+__global__ void k_seam_decide(PixGeom g, SeamGeom sg, const uint32_t *label, const int32_t *slot_of_id,
+                              const int64_t *S, const int64_t *n, const uint32_t *rid,
+                              const int32_t *seam_list, const int32_t *nseam, int32_t seam_cap, uint8_t *split,
+                              double *split_key, uint32_t *split_from, int32_t *err)
+{
+    int lane = threadIdx.x & 31;
+    int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    int ns = min(*nseam, seam_cap);
+    if (*nseam > seam_cap && blockIdx.x == 0 && threadIdx.x == 0) atomicExch(err, 0x5345414d);  // seam list overflow
+    int nn = sg.conn == 8 ? 8 : 4;
+    for (int64_t t = warp; t < ns; t += nwarps) {
+        int64_t p = seam_list[t];
+        int y = (int)(p / g.cols), x = (int)(p % g.cols);
+        int32_t par; int qd;
+        parent_and_quad(sg, y, x, par, qd);
+        const uint16_t *xp = g.img + p * g.B;
+        int64_t R = slot_of_id[label[p] - 1];
+        double kr = warp_key_pixel(xp, S + R * g.Bs, n[R], g.B, err);
+        double best = __longlong_as_double(0x7FF0000000000000ll);
+        int64_t seen[8];
+        int nseen = 0;
+        for (int k = 0; k < nn; k++) {
+            int yy = y + nb_dy(sg.conn, k), xx = x + nb_dx(sg.conn, k);
+            if (yy < 0 || yy >= g.rows || xx < 0 || xx >= g.cols) continue;
+            int64_t q = (int64_t)yy * g.cols + xx;
+            if (!label[q]) continue;
+            int32_t par2; int qd2;
+            parent_and_quad(sg, yy, xx, par2, qd2);
+            if (par2 != par || qd2 == qd) continue;
+            int64_t Q = slot_of_id[label[q] - 1];
+            bool dup = false;
+            for (int i = 0; i < nseen; i++) dup |= (seen[i] == Q);
+            if (dup) continue;
+            seen[nseen++] = Q;
+            double kq = warp_key_pixel(xp, S + Q * g.Bs, n[Q], g.B, err);
+            best = fmin(best, kq);
+        }
+        if (lane == 0) {
+            bool sp = best < kr;
+            split[p] = sp ? 1 : 0;
+            if (sp) { split_key[p] = kr; split_from[p] = rid[R]; }
+        }
+    }
+}
+
+// Apply every split together: the pixel leaves its region (exact integer
+// subtraction) and becomes a one-pixel region with ID p+1.
+__global__ void k_seam_apply(PixGeom g, uint32_t *label, const int32_t *slot_of_id, int64_t *S, int64_t *n,
+                             uint32_t *rid, uint8_t *lostid, const int32_t *seam_list, const int32_t *nseam,
+                             int32_t seam_cap, const uint8_t *split)
+{
+    int lane = threadIdx.x & 31;
+    int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    int ns = min(*nseam, seam_cap);
+    for (int64_t t = warp; t < ns; t += nwarps) {
+        int64_t p = seam_list[t];
+        if (!split[p]) continue;
+        int64_t R = slot_of_id[label[p] - 1];
+        const uint16_t *xp = g.img + p * g.B;
+        for (int b = lane; b < g.B; b += 32)
+            atomicAdd((unsigned long long *)&S[R * g.Bs + b], (unsigned long long)(-(long long)xp[b]));
+        if (lane == 0) {
+            atomicAdd((unsigned long long *)&n[R], (unsigned long long)(-1ll));
+            if (rid[R] == (uint32_t)(p + 1)) lostid[R] = 1;
+        }
+    }
+}
+
+// Split pixels carry their own ID from now on.
+__global__ void k_seam_label_singletons(const int32_t *seam_list, const int32_t *nseam, int32_t seam_cap,
+                                        const uint8_t *split, uint32_t *label)
+{
+    int ns = min(*nseam, seam_cap);
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < ns; t += gridDim.x * blockDim.x) {
+        int64_t p = seam_list[t];
+        if (split[p]) label[p] = (uint32_t)(p + 1);
+    }
+}
+
+// Regions that lost the pixel carrying their ID get ID = 1 + smallest
+// raster index of the pixels they keep (reading R5).
+__global__ void k_lost_reset(int64_t nslots, const uint8_t *lostid, uint32_t *rid)
+{
+    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < nslots; g += (int64_t)gridDim.x * blockDim.x)
+        if (lostid[g]) rid[g] = 0xffffffffu;
+}
+
+__global__ void k_lost_min(int64_t P, const uint32_t *label, const uint8_t *split, const int32_t *slot_of_id,
+                           const uint8_t *lostid, uint32_t *rid)
+{
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < P; p += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t l = label[p];
+        if (!l || split[p]) continue;
+        int64_t g = slot_of_id[l - 1];
+        if (lostid[g]) atomicMin(&rid[g], (uint32_t)(p + 1));
+    }
+}
+
+__global__ void k_lost_relabel(int64_t P, uint32_t *label, const uint8_t *split, const int32_t *slot_of_id,
+                               const uint8_t *lostid, const uint32_t *rid)
+{
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < P; p += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t l = label[p];
+        if (!l || split[p]) continue;
+        int64_t g = slot_of_id[l - 1];
+        if (lostid[g]) label[p] = rid[g];
+    }
+}
+
+// Region sources of the next level: surviving regions (by their possibly
+// re-derived ID) and the one-pixel regions of the seam pass.
+__global__ void k_mark_ids_upper(const int64_t *roff_prev, const SecState *st_prev,
+                                 int32_t nsec_prev, const uint8_t *alive, const int64_t *n, const uint32_t *rid,
+                                 uint8_t *isid, int32_t *srcslot)
+{
+    int sec = blockIdx.y;
+    if (sec >= nsec_prev) return;
+    int m0 = st_prev[sec].m0;
+    int64_t ro = roff_prev[sec];
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m0; i += gridDim.x * blockDim.x) {
+        int64_t gsl = ro + i;
+        if (!alive[gsl] || n[gsl] <= 0) continue;
+        uint32_t id = rid[gsl];
+        isid[id - 1] = 1;
+        srcslot[id - 1] = (int32_t)gsl;
+    }
+}
+
+__global__ void k_mark_singletons(const int32_t *seam_list, const int32_t *nseam, int32_t seam_cap,
+                                  const uint8_t *split, uint8_t *isid, int32_t *srcslot)
+{
+    int ns = min(*nseam, seam_cap);
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < ns; t += gridDim.x * blockDim.x) {
+        int64_t p = seam_list[t];
+        if (!split[p]) continue;
+        isid[p] = 1;
+        srcslot[p] = -1;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Root hierarchy snapshots (reading R9)
+// ---------------------------------------------------------------------------
+
+// canon[g] = 1-based rank (slot order = ID order) of slots alive after
+// merge ordinal M, 0 otherwise.  Single block.
+__global__ void k_snap_canon(int m0, const int32_t *absorbed_at, int32_t M, int32_t *canon, int32_t *R_out)
+{
+    __shared__ int32_t wcnt[32];
+    __shared__ int32_t base;
+    if (threadIdx.x == 0) base = 0;
+    __syncthreads();
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int c = 0; c < m0; c += blockDim.x) {
+        int i = c + threadIdx.x;
+        int f = (i < m0) ? (absorbed_at[i] > M) : 0;
+        unsigned bal = __ballot_sync(0xffffffffu, f);
+        if (lane == 0) wcnt[wid] = __popc(bal);
+        __syncthreads();
+        int off = 0, tot = 0;
+        for (int k = 0; k < nw; k++) { if (k < wid) off += wcnt[k]; tot += wcnt[k]; }
+        if (i < m0) canon[i] = f ? base + off + __popc(bal & ((1u << lane) - 1)) + 1 : 0;
+        __syncthreads();
+        if (threadIdx.x == 0) base += tot;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *R_out = base;
+}
+
+__device__ __forceinline__ int32_t snap_walk(int32_t g, const int32_t *parent, const int32_t *absorbed_at, int32_t M)
+{
+    for (int it = 0; it < (1 << 30) && absorbed_at[g] <= M; it++) g = parent[g];
+    return g;
+}
+
+__global__ void k_snap_labels(int64_t P, const uint32_t *label, const int32_t *slot_of_id, const int32_t *parent,
+                              const int32_t *absorbed_at, int32_t M, const int32_t *canon, int32_t *out)
+{
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < P; p += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t l = label[p];
+        out[p] = l ? canon[snap_walk(slot_of_id[l - 1], parent, absorbed_at, M)] : 0;
+    }
+}
+
+__global__ void k_snap_tables(int m0, int B, int Bs, const int64_t *S0, const int64_t *n0, const int32_t *parent,
+                              const int32_t *absorbed_at, int32_t M, const int32_t *canon, int64_t *sums,
+                              int64_t *counts)
+{
+    int lane = threadIdx.x & 31;
+    int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t g0 = warp; g0 < m0; g0 += nwarps) {
+        int c = canon[snap_walk((int32_t)g0, parent, absorbed_at, M)] - 1;
+        for (int b = lane; b < B; b += 32)
+            atomicAdd((unsigned long long *)&sums[(int64_t)c * B + b], (unsigned long long)S0[g0 * Bs + b]);
+        if (lane == 0) atomicAdd((unsigned long long *)&counts[c], (unsigned long long)n0[g0]);
+    }
+}
+
+}  // namespace rhseg

@@ -1,0 +1,86 @@
+"""Parity at the full workload sizes.
+
+145x145x200 (L=3): the whole run is compared with the oracle (about 40 s of
+CPU), for the FP64 screen and the FP16 tensor-core screen.
+1024x1024x224 (L=5, the benchmark's workload, same launch configuration as
+bench.py): the oracle cannot replay the whole recursion in test time, so the
+first iterations of sampled deepest-level sections (which are independent of
+each other) are compared record by record, and properties that hold at any
+size are checked on the final output."""
+import os
+import sys
+
+import numpy as np
+import pytest
+
+sys.path.insert(0, os.path.dirname(__file__))
+import synth  # noqa: E402
+from test_gpu_parity import _assert_same  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def P():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+    import paper_2106_12942_b300 as P
+    return P
+
+
+@pytest.fixture(scope="module")
+def cfg2(orc):
+    img, mask = synth.make(2)
+    kw = {k: v for k, v in synth.WORKLOADS[2].params.items() if k != "precision"}
+    return img, mask, kw, orc.run(img, mask, **kw)
+
+
+@pytest.mark.parametrize("precision", [1, 3, 0])
+def test_rhseg_145x145x200(P, cfg2, precision):
+    img, mask, kw, ref = cfg2
+    seg = P.RHSEG(img, mask, precision=precision, **kw)
+    seg.run()
+    _assert_same(seg, ref, f"145x145x200 p{precision}")
+    st = seg.stats()
+    if precision in (1, 2):
+        assert st["candidates"] <= st["screened_pairs"]
+
+
+@pytest.fixture(scope="module")
+def cfg4():
+    img, mask = synth.make(4)
+    kw = {k: v for k, v in synth.WORKLOADS[4].params.items()}
+    return img, mask, kw
+
+
+def test_rhseg_1024x1024x224_sampled(P, orc, cfg4):
+    img, mask, kw = cfg4
+    seg = P.RHSEG(img, mask, **kw)
+    seg.run()
+    log = seg.log()
+    L = kw["rnb_levels"]
+    okw = {k: v for k, v in kw.items() if k != "precision"}
+    iters = 200
+    for s in (0, 137, 255):
+        ref = orc.hseg_leaf(img, mask, s, max_iters=iters, **okw)
+        part = log[(log["level"] == L) & (log["section"] == s)][:len(ref.log)]
+        assert len(ref.log) > 0
+        for f in ["step", "kind", "survivor_id", "absorbed_id", "nregions_after"]:
+            assert np.array_equal(part[f], ref.log[f]), (s, f)
+        assert np.array_equal(part["key"].view(np.uint64), ref.log["key"].view(np.uint64)), s
+    # properties of the final output
+    lab, sums, cnt = seg.level(seg.n_levels() - 1)
+    unm = mask == 0
+    assert np.all((lab == 0) == ~unm)
+    R = len(cnt)
+    assert R == kw["conv_nregions"] or seg.stats()["stalled_sections"] > 0
+    nz = lab[lab > 0]
+    assert np.array_equal(np.bincount(nz, minlength=R + 1)[1:], cnt)
+    assert np.array_equal(sums.sum(0), img[unm].astype(np.int64).sum(0))
+    flat = lab.ravel()
+    _, first = np.unique(flat[flat > 0], return_index=True)
+    assert np.all(np.diff(first) > 0)
+    mg = log[log["kind"] != 2]
+    assert np.all(mg["survivor_id"] < mg["absorbed_id"])
+    assert np.array_equal(log["dissim"], np.sqrt(log["key"]))
