@@ -183,6 +183,14 @@ int rhseg_keys(const int64_t *S, const int64_t *n, int32_t nreg, int32_t bands, 
 int rhseg_div_rn(const uint64_t *n_hi, const uint64_t *n_lo, const uint64_t *d_hi,
                  const uint64_t *d_lo, int32_t n, double *out, void *cuda_stream);
 
+/* Diagnostic of the tensor-core screen's contraction: G = X X^T in FP32 for
+ * X = [rows][Bpad] FP16 (precision 1) or BF16 (precision 2) device rows,
+ * rows a multiple of 128, Bpad a multiple of 64; G [rows][rows] device
+ * float.  Uses the same TMA/tcgen05 main loop as the spectral screen
+ * (Section 4.2's spectral kernel, here as a Gram contraction).  Does not
+ * wait. */
+int rhseg_gram_tc(const void *X, int32_t rows, int32_t Bpad, int32_t precision, float *G, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

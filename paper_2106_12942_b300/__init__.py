@@ -7,4 +7,4 @@ loads the library on first use and raises if it has not been built (there
 is no fallback implementation).
 """
 from ._abi import MERGE_DTYPE, load  # noqa: F401
-from .rhseg import RHSEG, RHSEGError, div_rn, keys, make_params  # noqa: F401
+from .rhseg import RHSEG, RHSEGError, div_rn, gram_tc, keys, make_params  # noqa: F401

@@ -69,6 +69,7 @@ SIGNATURES = {
     "rhseg_last_cuda_error": (C.c_char_p, []),
     "rhseg_keys": (C.c_int, [_VP, _VP, C.c_int32, C.c_int32, C.c_int32, _VP, _VP, C.c_int32, _VP, _VP]),
     "rhseg_div_rn": (C.c_int, [_VP, _VP, _VP, _VP, C.c_int32, _VP, _VP]),
+    "rhseg_gram_tc": (C.c_int, [_VP, C.c_int32, C.c_int32, C.c_int32, _VP, _VP]),
 }
 
 _lib = None

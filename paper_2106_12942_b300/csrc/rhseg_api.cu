@@ -170,6 +170,8 @@ struct rhseg_handle {
     // instrumentation
     int64_t nlaunch = 0, nscreen = 0;
     std::vector<cudaEvent_t> prof_ev;   // [3 kernels][chunk][2]
+    CUtensorMap tmap;                   // operand rows of the tensor-core screen
+    cudaError_t launch_err = cudaSuccess;
 };
 
 static int check_params(const rhseg_params *p, int32_t rows, int32_t cols, int32_t bands)
@@ -379,6 +381,13 @@ static int common_create(rhseg_handle *h, const rhseg_params *p, void *stream)
         if ((rc = h->Af.alloc(h->npos))) return rc;
         if ((rc = h->kf.alloc(h->npos))) return rc;
     }
+    if (screen_uses_tcgen05(p->precision)) {
+        int mr = make_operand_map(&h->tmap, h->X.p, (int64_t)h->npos, h->Bpad, p->precision);
+        if (mr) {
+            snprintf(g_cuda_msg, sizeof(g_cuda_msg), "tensor map for the screen operands failed (%d)", mr);
+            return RHSEG_ECUDA;
+        }
+    }
     int nsec_max = h->geo[p->rnb_levels].nsec;
     if ((rc = h->st.alloc(nsec_max))) return rc;
     if ((rc = h->aoff.alloc(nsec_max + 1))) return rc;
@@ -574,7 +583,12 @@ static void launch_screen(rhseg_handle *h, const LevelDev &L)
     switch (h->p.precision) {
     case 0: k_screen_simt<double, double><<<grid, 256, 0, h->stream>>>(L); break;
     case 3: k_screen_simt<float, float><<<grid, 256, 0, h->stream>>>(L); break;
-    default: launch_screen_tc(L, h->p.precision, h->n_sm, h->stream); break;
+    default: {
+        TcJob job{0, nullptr};
+        cudaError_t e = launch_screen_tc_map(L, h->tmap, h->p.precision, h->n_sm * 2, h->stream, job);
+        if (e != cudaSuccess) h->launch_err = e;
+        break;
+    }
     }
 }
 
@@ -726,6 +740,7 @@ static int run_impl(rhseg_handle *h)
                 }
             }
             CK(cudaGetLastError());
+            CK(h->launch_err);
             it += chunk;
             k_count_active<<<1, 1024, 0, s>>>(h->st.p, G.nsec, h->active.p); h->nlaunch++;
             CK(cudaMemcpyAsync(h->active_host, h->active.p, 4, cudaMemcpyDeviceToHost, s));
@@ -1031,6 +1046,25 @@ __global__ void k_div(const uint64_t *nh, const uint64_t *nl, const uint64_t *dh
         if ((D.lo | D.hi) == 0 || (N.hi >> 63) || (D.hi >> 63)) { out[t] = __longlong_as_double(0x7FF8000000000000ll); continue; }
         out[t] = div_rn_u128(N, D, nullptr);
     }
+}
+
+extern "C" int rhseg_gram_tc(const void *X, int32_t rows, int32_t Bpad, int32_t precision, float *G,
+                             void *cuda_stream)
+{
+    if (!X || !G || rows <= 0 || rows % TC_TILE || Bpad <= 0 || Bpad % TC_KATOM || (precision != 1 && precision != 2))
+        return RHSEG_EINVAL;
+    CUtensorMap map;
+    if (make_operand_map(&map, X, rows, Bpad, precision)) {
+        snprintf(g_cuda_msg, sizeof(g_cuda_msg), "tensor map encode failed");
+        return RHSEG_ECUDA;
+    }
+    LevelDev L{};
+    L.Bpad = Bpad;
+    L.nsec = 1;
+    TcJob job{rows, G};
+    int nb = rows / TC_TILE;
+    CK(launch_screen_tc_map(L, map, precision, std::min(nb * nb, 296), (cudaStream_t)cuda_stream, job));
+    return RHSEG_OK;
 }
 
 extern "C" int rhseg_div_rn(const uint64_t *n_hi, const uint64_t *n_lo, const uint64_t *d_hi, const uint64_t *d_lo,

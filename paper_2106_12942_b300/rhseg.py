@@ -174,3 +174,16 @@ def div_rn(n_hi, n_lo, d_hi, d_lo, stream=None):
                           C.c_void_p(d_lo.data_ptr()), n_hi.numel(), C.c_void_p(out.data_ptr()),
                           _stream_ptr(stream)), "rhseg_div_rn")
     return out
+
+
+def gram_tc(X, precision=1, stream=None):
+    """G = X X^T (FP32) of 16-bit rows on the tensor cores (diagnostic of the
+    screen's contraction).  X: CUDA tensor float16/bfloat16 [rows, Bpad],
+    rows % 128 == 0, Bpad % 64 == 0."""
+    import torch
+    L = _abi.load()
+    X = X.contiguous()
+    G = torch.empty(X.shape[0], X.shape[0], dtype=torch.float32, device=X.device)
+    _check(L.rhseg_gram_tc(C.c_void_p(X.data_ptr()), X.shape[0], X.shape[1], precision, C.c_void_p(G.data_ptr()),
+                           _stream_ptr(stream)), "rhseg_gram_tc")
+    return G
