@@ -157,6 +157,33 @@ int rhseg_n_levels(const rhseg_handle *h, int32_t *n_levels);
 int rhseg_get_level(rhseg_handle *h, int32_t level, int32_t *labels, int64_t *band_sums,
                     int64_t *counts, int32_t *nregions_out);
 
+/* Largest root-level region count rhseg_get_level_noalloc accepts. */
+#define RHSEG_NOALLOC_MAX_REGIONS 65536
+
+/* Same result as rhseg_get_level, written straight into caller-owned DEVICE
+ * buffers, for callers that may not allocate device memory once they are
+ * running: for example a service that reserves its whole device-memory
+ * budget at start-up, or code embedded in a framework whose allocator owns
+ * all of the device memory.  This call makes no device allocation of any
+ * kind; the handle's own buffers were allocated by rhseg_create and
+ * rhseg_run before.  The paper has no counterpart (it is an interface
+ * choice of this library).
+ *   labels_dev    [rows*cols] int32 or NULL
+ *   band_sums_dev [regions_cap*bands] int64 or NULL (cleared, then filled)
+ *   counts_dev    [regions_cap] int64 or NULL (cleared, then filled)
+ *   nregions_out  host int32: R of this level (may be NULL)
+ * RHSEG_ETRUNC if R > regions_cap while sums or counts are requested (R is
+ * still returned).  The working array (one int32 per root region) is a
+ * fixed, file-scope device array of RHSEG_NOALLOC_MAX_REGIONS + 1 entries
+ * that every GPU using the library holds until the process exits; a root
+ * level that started with more regions is rejected with RHSEG_ERANGE.  The
+ * first call on a device looks up that array's device address once, so
+ * make the first call before any stream capture.  All calls share the one
+ * array: calls that overlap on the GPU (other host threads, other streams)
+ * race on it.  Runs on the handle's stream and waits for completion. */
+int rhseg_get_level_noalloc(rhseg_handle *h, int32_t level, int32_t *labels_dev, int64_t *band_sums_dev,
+                            int64_t *counts_dev, int32_t regions_cap, int32_t *nregions_out);
+
 /* Full canonical merge log into host `log` (capacity log_cap records).
  * *log_len receives the number of records; RHSEG_ETRUNC if log_cap is
  * smaller (nothing written).  log may be NULL to query the length. */

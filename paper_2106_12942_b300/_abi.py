@@ -12,6 +12,7 @@ SO_PATH = os.path.join(HERE, "librhseg_b300.so")
 
 RHSEG_OK, RHSEG_EINVAL, RHSEG_ERANGE, RHSEG_ENOMEM = 0, -1, -2, -3
 RHSEG_ECUDA, RHSEG_ETIMEOUT, RHSEG_ESTATE, RHSEG_ETRUNC, RHSEG_EDEVICE = -4, -5, -6, -7, -8
+RHSEG_NOALLOC_MAX_REGIONS = 65536
 
 
 class Params(C.Structure):
@@ -63,6 +64,7 @@ SIGNATURES = {
     "rhseg_n_levels": (C.c_int, [_VP, C.POINTER(C.c_int32)]),
     "rhseg_get_level": (C.c_int, [_VP, C.c_int32, _VP, _VP, _VP, C.POINTER(C.c_int32)]),
     "rhseg_get_log": (C.c_int, [_VP, _VP, C.c_int64, C.POINTER(C.c_int64)]),
+    "rhseg_get_level_noalloc": (C.c_int, [_VP, C.c_int32, _VP, _VP, _VP, C.c_int32, C.POINTER(C.c_int32)]),
     "rhseg_get_stats": (C.c_int, [_VP, C.POINTER(Stats)]),
     "rhseg_destroy": (None, [_VP]),
     "rhseg_strerror": (C.c_char_p, [C.c_int]),

@@ -15,6 +15,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <mutex>
 #include <vector>
 
 #include <cuda_fp16.h>
@@ -890,6 +891,92 @@ extern "C" int rhseg_get_level(rhseg_handle *h, int32_t level, int32_t *labels, 
         CK(cudaGetLastError());
         if (band_sums) CK(cudaMemcpyAsync(band_sums, h->snap_sums.p, (size_t)R * h->B * 8, cudaMemcpyDeviceToHost, s));
         if (counts) CK(cudaMemcpyAsync(counts, h->snap_counts.p, (size_t)R * 8, cudaMemcpyDeviceToHost, s));
+    }
+    CK(cudaStreamSynchronize(s));
+    return RHSEG_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Hierarchy levels without device allocation
+// ---------------------------------------------------------------------------
+
+// Working array of rhseg_get_level_noalloc: canonical label of each root
+// region, then the region count.  File scope, so it needs no allocation.
+static __device__ __align__(256) int32_t g_level_scratch[RHSEG_NOALLOC_MAX_REGIONS + 1];
+
+static int32_t *g_level_scratch_dev[64];     // device address per device, looked up once
+static std::mutex g_level_scratch_mu;
+
+static int level_scratch_ptr(int32_t **out)
+{
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return RHSEG_EDEVICE;
+    std::lock_guard<std::mutex> lock(g_level_scratch_mu);
+    if (!g_level_scratch_dev[dev]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_level_scratch);
+        if (e != cudaSuccess || !p) {
+            snprintf(g_cuda_msg, sizeof(g_cuda_msg), "cudaGetSymbolAddress(level scratch): %s", cudaGetErrorString(e));
+            return RHSEG_ECUDA;
+        }
+        g_level_scratch_dev[dev] = (int32_t *)p;
+    }
+    *out = g_level_scratch_dev[dev];
+    return RHSEG_OK;
+}
+
+extern "C" int rhseg_get_level_noalloc(rhseg_handle *h, int32_t level, int32_t *labels_dev, int64_t *band_sums_dev,
+                                       int64_t *counts_dev, int32_t regions_cap, int32_t *nregions_out)
+{
+    if (!h || regions_cap < 0) return RHSEG_EINVAL;
+    if (!h->ran) return RHSEG_ESTATE;
+    if (level < 0 || level >= (int32_t)h->targets.size()) return RHSEG_EINVAL;
+    int m0 = h->root_m0;
+    if (m0 > RHSEG_NOALLOC_MAX_REGIONS) {
+        snprintf(g_cuda_msg, sizeof(g_cuda_msg),
+                 "root level has %d regions; rhseg_get_level_noalloc holds at most %d", m0, RHSEG_NOALLOC_MAX_REGIONS);
+        return RHSEG_ERANGE;
+    }
+    int32_t *scratch = nullptr;
+    int rc = level_scratch_ptr(&scratch);
+    if (rc) return rc;
+    int32_t *canon = scratch, *Rdev = scratch + RHSEG_NOALLOC_MAX_REGIONS;
+    cudaStream_t s = h->stream;
+    int64_t P = (int64_t)h->rows * h->cols;
+    int64_t M = (int64_t)h->root_m0 - h->targets[level];
+    if (M > h->root_nmerge) M = h->root_nmerge;
+    if (M < 0) M = 0;
+    SlotSet &T = h->slots[(h->p.rnb_levels - 1) & 1];   // tables of the root level
+    k_snap_canon<<<1, 1024, 0, s>>>(m0, T.absorbed_at.p, (int32_t)M, canon, Rdev);
+    CK(cudaGetLastError());
+    int32_t R = 0;
+    CK(cudaMemcpyAsync(&R, Rdev, 4, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (nregions_out) *nregions_out = R;
+    if (labels_dev) {
+        k_snap_labels<<<h->n_sm * 8, 256, 0, s>>>(P, h->label.p, h->slot_of_id.p, T.parent.p, T.absorbed_at.p,
+                                                  (int32_t)M, canon, labels_dev);
+        CK(cudaGetLastError());
+    }
+    if (band_sums_dev || counts_dev) {
+        if (R > regions_cap) {
+            CK(cudaStreamSynchronize(s));
+            return RHSEG_ETRUNC;
+        }
+        if (band_sums_dev && R > 0) CK(cudaMemsetAsync(band_sums_dev, 0, (size_t)R * h->B * 8, s));
+        if (counts_dev && R > 0) CK(cudaMemsetAsync(counts_dev, 0, (size_t)R * 8, s));
+        if (band_sums_dev && counts_dev) {
+            k_snap_tables<<<h->n_sm * 4, 256, 0, s>>>(m0, h->B, h->Bs, h->S0.p, h->n0.p, T.parent.p, T.absorbed_at.p,
+                                                      (int32_t)M, canon, band_sums_dev, counts_dev);
+            CK(cudaGetLastError());
+        } else if (R > 0) {
+            // only one of the two tables was requested
+            k_snap_tables_part<<<h->n_sm * 4, 256, 0, s>>>(m0, h->B, h->Bs, h->S0.p, h->n0.p, T.parent.p,
+                                                           T.absorbed_at.p, (int32_t)M, canon, band_sums_dev,
+                                                           counts_dev);
+            CK(cudaGetLastError());
+        }
     }
     CK(cudaStreamSynchronize(s));
     return RHSEG_OK;

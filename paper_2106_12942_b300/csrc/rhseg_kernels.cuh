@@ -1054,4 +1054,22 @@ __global__ void k_snap_tables(int m0, int B, int Bs, const int64_t *S0, const in
     }
 }
 
+// As k_snap_tables, for a caller that wants only the band sums or only the
+// counts (the other pointer is null).
+__global__ void k_snap_tables_part(int m0, int B, int Bs, const int64_t *S0, const int64_t *n0, const int32_t *parent,
+                                   const int32_t *absorbed_at, int32_t M, const int32_t *canon, int64_t *sums,
+                                   int64_t *counts)
+{
+    int lane = threadIdx.x & 31;
+    int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t g0 = warp; g0 < m0; g0 += nwarps) {
+        int c = canon[snap_walk((int32_t)g0, parent, absorbed_at, M)] - 1;
+        if (sums)
+            for (int b = lane; b < B; b += 32)
+                atomicAdd((unsigned long long *)&sums[(int64_t)c * B + b], (unsigned long long)S0[g0 * Bs + b]);
+        if (counts && lane == 0) atomicAdd((unsigned long long *)&counts[c], (unsigned long long)n0[g0]);
+    }
+}
+
 }  // namespace rhseg
