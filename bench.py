@@ -93,10 +93,14 @@ class ClockSampler:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
-def workload(k):
+def workload(k, rows=None, cols=None):
     import synth
     w = synth.WORKLOADS[k]
-    img, mask = synth.make(k)
+    img, mask = synth.make(k, rows=rows, cols=cols)
+    if rows or cols:
+        import dataclasses
+        w = dataclasses.replace(w, name=f"{w.name}_crop{img.shape[0]}x{img.shape[1]}", rows=img.shape[0],
+                                cols=img.shape[1])
     return w, img, mask
 
 
@@ -163,6 +167,9 @@ def main():
     ap.add_argument("--precision", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--rows", type=int, default=None, help="scaled-down image (profiling); not a bench line")
+    ap.add_argument("--cols", type=int, default=None)
+    ap.add_argument("--levels", type=int, default=None)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -178,8 +185,10 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
-    w, img, mask = workload(args.workload)
+    w, img, mask = workload(args.workload, args.rows, args.cols)
     params = dict(w.params)
+    if args.levels is not None:
+        params["rnb_levels"] = args.levels
     if args.precision is not None:
         params["precision"] = args.precision
     params["profile"] = 1
@@ -257,6 +266,8 @@ def main():
                       "spec_step": sum(s["spec_ms"] for s in stats) / args.steps},
         "screen": {"screened_pairs": stats[-1]["screened_pairs"], "candidates": stats[-1]["candidates"],
                    "fallbacks": stats[-1]["fallbacks"]},
+        "level_ms": [round(x, 2) for x in stats[-1]["level_ms"][:params["rnb_levels"]]],
+        "level_iters": stats[-1]["level_iters"][:params["rnb_levels"]],
     }
 
     if not args.no_e2e:

@@ -115,6 +115,10 @@ typedef struct rhseg_stats {
     int32_t screen_impl;      /* 0 none, 1 FP64 CUDA cores, 2 FP32-accumulate CUDA
                                  cores, 3 tcgen05 tensor cores                    */
     int32_t pad;
+    double  level_ms[6];      /* device time of each recursion level (index
+                                 level-1), set-up and HSEG iterations             */
+    int32_t level_iters[6];   /* HSEG iterations run at each level (max over
+                                 its sections)                                    */
 } rhseg_stats;
 
 typedef struct rhseg_handle rhseg_handle;

@@ -42,6 +42,7 @@ class Stats(C.Structure):
         ("kernel_launches", C.c_int64), ("screen_launches", C.c_int64),
         ("screen_ms", C.c_double), ("adj_ms", C.c_double), ("spec_ms", C.c_double),
         ("screen_impl", C.c_int32), ("pad", C.c_int32),
+        ("level_ms", C.c_double * 6), ("level_iters", C.c_int32 * 6),
     ]
 
 

@@ -620,7 +620,11 @@ static int run_impl(rhseg_handle *h)
     CK(cudaGetLastError());
     CK(cudaMemsetAsync(h->split.p, 0, P, s));
     int cur = 0;
+    cudaEvent_t lev_ev[2];
+    CK(cudaEventCreate(&lev_ev[0]));
+    CK(cudaEventCreate(&lev_ev[1]));
     for (int lev = L; lev >= 1; lev--) {
+        CK(cudaEventRecord(lev_ev[0], s));
         LevelGeo &G = h->geo[lev];
         auto &GI = h->geo_i32[lev];
         auto &GJ = h->geo_i64[lev];
@@ -783,8 +787,20 @@ static int run_impl(rhseg_handle *h)
             h->stats.seam_splits += q.nsplit;
         }
         if (lev == 1) h->root_nmerge = sth[0].nmerge;
+        {
+            int32_t mi = 0;
+            for (int k = 0; k < G.nsec; k++) mi = std::max(mi, sth[k].iter);
+            h->stats.level_iters[lev - 1] = mi;
+            CK(cudaEventRecord(lev_ev[1], s));
+            CK(cudaEventSynchronize(lev_ev[1]));
+            float lms = 0;
+            CK(cudaEventElapsedTime(&lms, lev_ev[0], lev_ev[1]));
+            h->stats.level_ms[lev - 1] = lms;
+        }
         cur ^= 1;
     }
+    cudaEventDestroy(lev_ev[0]);
+    cudaEventDestroy(lev_ev[1]);
     CK(cudaEventRecord(ev1, s));
     CK(cudaEventSynchronize(ev1));
     float ms = 0;

@@ -130,7 +130,11 @@ class RHSEG:
     def stats(self) -> dict:
         s = _abi.Stats()
         _check(self._lib.rhseg_get_stats(self._h, C.byref(s)), "rhseg_get_stats")
-        return {f: getattr(s, f) for f, _ in _abi.Stats._fields_}
+        out = {}
+        for f, _ in _abi.Stats._fields_:
+            v = getattr(s, f)
+            out[f] = list(v) if hasattr(v, "__len__") else v
+        return out
 
     def close(self):
         if self._h:
