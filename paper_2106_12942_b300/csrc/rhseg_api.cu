@@ -142,7 +142,7 @@ struct rhseg_handle {
     // positions
     DBuf<int32_t> slot_of_pos;
     DBuf<uint8_t> X;
-    DBuf<float> Af, kf;
+    DBuf<float> Af, kf, H;
     DBuf<double> Ad, kd;
     size_t npos = 0;
     // per level, sized at run time
@@ -382,6 +382,8 @@ static int common_create(rhseg_handle *h, const rhseg_params *p, void *stream)
         if ((rc = h->Af.alloc(h->npos))) return rc;
         if ((rc = h->kf.alloc(h->npos))) return rc;
     }
+    if (p->precision == 1 || p->precision == 2)
+        if ((rc = h->H.alloc(h->npos))) return rc;
     if (screen_uses_tcgen05(p->precision)) {
         int mr = make_operand_map(&h->tmap, h->X.p, (int64_t)h->npos, h->Bpad, p->precision);
         if (mr) {
@@ -714,6 +716,7 @@ static int run_impl(rhseg_handle *h)
         D.absorbed_at = T.absorbed_at.p; D.bestK = T.bestK.p; D.bestP = T.bestP.p; D.pos_of_slot = T.pos_of_slot.p;
         D.slot_of_pos = h->slot_of_pos.p; D.X = h->X.p;
         D.Af = h->Af.p; D.kf = h->kf.p; D.Ad = h->Ad.p; D.kd = h->kd.p;
+        D.H = (h->p.precision == 1 || h->p.precision == 2) ? h->H.p : nullptr;
         D.adj = h->adj.p; D.cand = h->cand.p; D.cand_cap = cand_cap;
         D.log = h->log.p; D.err = h->err.p;
         k_init_best<<<dim3(std::max(1, std::min(64, ceil_div(m0max, 8))), G.nsec), 256, 0, s>>>(D); h->nlaunch++;
@@ -1077,7 +1080,7 @@ extern "C" void rhseg_destroy(rhseg_handle *h)
     h->srcslot.release(); h->slot_of_id.release(); h->seam_list.release(); h->nseam.release();
     h->split_key.release();
     h->slots[0].release(); h->slots[1].release();
-    h->slot_of_pos.release(); h->X.release(); h->Af.release(); h->kf.release(); h->Ad.release(); h->kd.release();
+    h->slot_of_pos.release(); h->X.release(); h->Af.release(); h->kf.release(); h->H.release(); h->Ad.release(); h->kd.release();
     h->adj.release(); h->aoff.release(); h->Wrow.release(); h->ref.release(); h->cand.release(); h->st.release();
     h->log.release(); h->err.release(); h->active.release();
     h->S0.release(); h->n0.release();

@@ -68,6 +68,7 @@ struct LevelDev {
     int32_t *slot_of_pos;
     void    *X;                // [npos][Bpad] half/bf16 (precision 1/2) or double (0)
     float   *Af;  float  *kf;  // screen row terms (precision 1/2)
+    float   *H;                // h_i = (A_i - T k_i) / 2 of the current step (tensor-core screen)
     double  *Ad;  double *kd;  // screen row terms (precision 0)
     // adjacency bitmaps
     uint32_t *adj;

@@ -392,38 +392,37 @@ struct StepSmem {
     int32_t rescan_overflow;
 };
 
-// Min over adjacent partners of slot r (exact keys), whole block.
-__device__ PairKey block_row_best(const LevelDev &L, int sec, int r, StepSmem &sm)
+// Exact best adjacent partner of slot r recomputed by one warp (the row's
+// words are read by the lanes, set bits visited in order, one key per bit).
+__device__ void warp_rescan_row(const LevelDev &L, int sec, int r)
 {
-    int64_t ro = L.roff[sec];
-    int W = L.W[sec];
+    const int lane = threadIdx.x & 31;
+    const int64_t ro = L.roff[sec];
+    const int W = L.W[sec];
     const uint32_t *row = L.adj + L.aoff[sec] + (int64_t)r * W;
     const int64_t *Sr = L.S + (ro + r) * L.Bs;
-    int64_t nr = L.n[ro + r];
-    int wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int64_t nr = L.n[ro + r];
     PairKey best = pk_none();
-    for (int w0 = 0; w0 < W; w0 += NB_CHUNK_WORDS) {
-        __syncthreads();
-        if (threadIdx.x == 0) sm.nnb = 0;
-        __syncthreads();
-        for (int w = w0 + threadIdx.x; w < min(W, w0 + NB_CHUNK_WORDS); w += blockDim.x) {
-            uint32_t bits = row[w];
+    for (int w0 = 0; w0 < W; w0 += 32) {
+        uint32_t word = (w0 + lane < W) ? row[w0 + lane] : 0u;
+        unsigned nz = __ballot_sync(0xffffffffu, word != 0);
+        while (nz) {
+            int src = __ffs(nz) - 1;
+            nz &= nz - 1;
+            uint32_t bits = __shfl_sync(0xffffffffu, word, src);
             while (bits) {
-                int q = w * 32 + __ffs(bits) - 1;
+                int q = (w0 + src) * 32 + __ffs(bits) - 1;
                 bits &= bits - 1;
-                sm.nb[atomicAdd(&sm.nnb, 1)] = q;
+                double K = warp_key(Sr, nr, L.S + (ro + q) * L.Bs, L.n[ro + q], L.B, L.err);
+                PairKey c = pk_make(dbits(K), r, q);
+                if (pk_less(c, best)) best = c;
             }
         }
-        __syncthreads();
-        int cnt = sm.nnb;
-        for (int t = wid; t < cnt; t += nw) {
-            int q = sm.nb[t];
-            double K = warp_key(Sr, nr, L.S + (ro + q) * L.Bs, L.n[ro + q], L.B, L.err);
-            PairKey c = pk_make(dbits(K), r, q);
-            if (pk_less(c, best)) best = c;
-        }
     }
-    return block_min_pk(best, sm.pk);
+    if (lane == 0) {
+        L.bestK[ro + r] = best.k;
+        L.bestP[ro + r] = (best.k == RHSEG_KEY_NONE) ? -1 : (int32_t)(best.lo == (uint32_t)r ? best.hi : best.lo);
+    }
 }
 
 // Merge slot b into slot a (a < b, so a keeps the smaller ID).  Whole block.
@@ -539,31 +538,28 @@ __device__ void block_merge(const LevelDev &L, int sec, int a, int b, double K, 
     int nres = min(sm.nrescan, RESCAN_CAP);
     int ovf = sm.rescan_overflow;
     if (!ovf) {
-        for (int k = 0; k < nres; k++) {
-            int r = sm.rescan[k];
-            PairKey rb = block_row_best(L, sec, r, sm);
-            if (tid == 0) {
-                L.bestK[ro + r] = rb.k;
-                L.bestP[ro + r] = (rb.k == RHSEG_KEY_NONE) ? -1 : (int32_t)(rb.lo == (uint32_t)r ? rb.hi : rb.lo);
+        // rows whose best partner was a or b: one warp per row
+        for (int k = wid; k < nres; k += nw) warp_rescan_row(L, sec, sm.rescan[k]);
+    } else {
+        // too many such rows to list: re-scan every neighbour of a
+        for (int w0 = 0; w0 < W; w0 += NB_CHUNK_WORDS) {
+            __syncthreads();
+            if (tid == 0) sm.nnb = 0;
+            __syncthreads();
+            for (int w = w0 + tid; w < min(W, w0 + NB_CHUNK_WORDS); w += nt) {
+                uint32_t bits = rowA[w];
+                while (bits) {
+                    int q = w * 32 + __ffs(bits) - 1;
+                    bits &= bits - 1;
+                    sm.nb[atomicAdd(&sm.nnb, 1)] = q;
+                }
             }
             __syncthreads();
-        }
-    } else {
-        // too many rows to re-scan one by one: re-scan every neighbour of a
-        for (int w = 0; w < W; w++) {
-            uint32_t bits = rowA[w];
-            while (bits) {
-                int r = w * 32 + __ffs(bits) - 1;
-                bits &= bits - 1;
-                PairKey rb = block_row_best(L, sec, r, sm);
-                if (tid == 0) {
-                    L.bestK[ro + r] = rb.k;
-                    L.bestP[ro + r] = (rb.k == RHSEG_KEY_NONE) ? -1 : (int32_t)(rb.lo == (uint32_t)r ? rb.hi : rb.lo);
-                }
-                __syncthreads();
-            }
+            int cnt = sm.nnb;
+            for (int k = wid; k < cnt; k += nw) warp_rescan_row(L, sec, sm.nb[k]);
         }
     }
+    __syncthreads();
     // screen rows of a (new features) and b (dead)
     int pa_pos = L.pos_of_slot[ro + a], pb_pos = L.pos_of_slot[ro + b];
     if (wid == 0) write_row_any(L, sec, a, pa_pos, sc);
@@ -655,6 +651,19 @@ __global__ void __launch_bounds__(STEP_THREADS) k_adj_step(LevelDev L, ScreenCon
         } else {
             st->spec_pending = 0;
             if (!merged) { st->stalled = 1; st->done = 1; }
+        }
+    }
+    // per-row threshold terms of this step's tensor-core screen
+    if (L.H != nullptr) {
+        __syncthreads();
+        if (st->spec_pending) {
+            const float Tf = __double2float_ru(st->tthr);
+            const int mc = st->mc;
+            const int pend = ((mc + 127) / 128) * 128;
+            const int64_t pb = L.poff[sec];
+            const float inf = __int_as_float(0x7f800000);
+            for (int pos = threadIdx.x; pos < pend; pos += blockDim.x)
+                L.H[pb + pos] = (pos < mc) ? 0.5f * (L.Af[pb + pos] - Tf * L.kf[pb + pos]) : inf;
         }
     }
 }

@@ -38,7 +38,7 @@ struct TcShared {
     uint64_t tfull[2], tempty[2];
     uint32_t tmem_base;
     int abort;
-    float hc[2][TC_TILE];
+    alignas(16) float hc[2][TC_TILE];
     long long pre[MAX_SECTIONS + 1];
 };
 constexpr int TC_SMEM_BYTES = TC_STAGES * TC_STAGE_BYTES + 1024 + (int)((sizeof(TcShared) + 127) / 128 * 128);
@@ -287,56 +287,75 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_screen_tc(LevelDev L, const _
         __syncwarp();
     } else {
         // ---------------- epilogue: warps 2..5 ----------------
+        // Each thread owns one accumulator row (TMEM lane).  The per-row
+        // terms h of the next tile are fetched while the current tile is
+        // tested; the test runs as max_j (g_ij - h_j) > h_i over 32 columns
+        // and only a passing chunk is examined element by element.
         const int q = warp & 3;                     // tensor-memory lane quarter of this warp
         const int row = q * 32 + lane;              // accumulator row = TMEM lane
         const int et = threadIdx.x - 64;            // 0..127, column index for h
+        const float inf = __int_as_float(0x7f800000);
         int tcount = 0;
+        float hc_next = inf, hr_next = inf;
+        {
+            int sec, I, J;
+            int64_t rowA, rowB;
+            if (job.gram_rows == 0 && tc_tile(L, job, sh.pre, blockIdx.x, total, sec, I, J, rowA, rowB)) {
+                hc_next = L.H[rowB + et];
+                hr_next = L.H[rowA + row];
+            }
+        }
         for (long long t = blockIdx.x;; t += gridDim.x, tcount++) {
             int sec = 0, I = 0, J = 0;
             int64_t rowA, rowB;
             bool have = tc_tile(L, job, sh.pre, t, total, sec, I, J, rowA, rowB);
             if (epi_bar_or(!have || *abort)) break;          // uniform over the 128 threads
-            int buf = tcount & 1;
-            float hr = 0.f;
-            SecState *st = nullptr;
-            if (job.gram_rows == 0) {
-                st = &L.st[sec];
-                int mc = st->mc;
-                int64_t pb = L.poff[sec];
-                float Tf = __double2float_ru(st->tthr);
-                const float inf = __int_as_float(0x7f800000);
-                int ci = J * TC_TILE + et;
-                sh.hc[buf][et] = (ci < mc) ? 0.5f * (L.Af[pb + ci] - Tf * L.kf[pb + ci]) : inf;
-                int ri = I * TC_TILE + row;
-                hr = (ri < mc) ? 0.5f * (L.Af[pb + ri] - Tf * L.kf[pb + ri]) : inf;
-            }
+            const int buf = tcount & 1;
+            sh.hc[buf][et] = hc_next;
+            const float hr = hr_next;
             asm volatile("bar.sync 1, 128;" ::: "memory");
+            if (job.gram_rows == 0) {
+                int s2, I2, J2;
+                int64_t rA2, rB2;
+                if (tc_tile(L, job, sh.pre, t + gridDim.x, total, s2, I2, J2, rA2, rB2)) {
+                    hc_next = L.H[rB2 + et];
+                    hr_next = L.H[rA2 + row];
+                }
+            }
             bool ok = mbar_wait(&sh.tfull[buf], (tcount >> 1) & 1, abort, L.err);
             ok = __all_sync(0xffffffffu, ok);
             if (!ok) continue;                               // the next loop top stops every warp
             tc_fence_after();
             const uint32_t taddr = tbase + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * TC_TILE);
-            const bool diag = (I == J);
-            for (int c0 = 0; c0 < TC_TILE; c0 += 32) {
-                uint32_t r[32];
-                tmem_ld32(taddr + (uint32_t)c0, r);
-                if (job.gram_rows > 0) {
+            if (job.gram_rows > 0) {
+                for (int c0 = 0; c0 < TC_TILE; c0 += 32) {
+                    uint32_t r[32];
+                    tmem_ld32(taddr + (uint32_t)c0, r);
                     float *o = job.gram_out + ((int64_t)I * TC_TILE + row) * job.gram_rows + (int64_t)J * TC_TILE + c0;
 #pragma unroll
                     for (int c = 0; c < 32; c++) o[c] = __uint_as_float(r[c]);
-                    continue;
                 }
+            } else {
+                SecState *st = &L.st[sec];
+                const bool diag = (I == J);
+                const float *hcs = sh.hc[buf];
+                for (int c0 = 0; c0 < TC_TILE; c0 += 32) {
+                    uint32_t r[32];
+                    tmem_ld32(taddr + (uint32_t)c0, r);
+                    float m = -inf;
 #pragma unroll
-                for (int c = 0; c < 32; c++) {
-                    int cc = c0 + c;
-                    bool pass = __uint_as_float(r[c]) > hr + sh.hc[buf][cc];
-                    if (diag && cc <= row) pass = false;
-                    if (pass) {
-                        uint32_t idx = atomicAdd(&st->ncand, 1u);
-                        if ((int64_t)idx < L.cand_cap) {
-                            uint32_t *cd = L.cand + ((int64_t)sec * L.cand_cap + idx) * 2;
-                            cd[0] = (uint32_t)(I * TC_TILE + row);
-                            cd[1] = (uint32_t)(J * TC_TILE + cc);
+                    for (int c = 0; c < 32; c++) m = fmaxf(m, __uint_as_float(r[c]) - hcs[c0 + c]);
+                    if (m > hr) {
+                        for (int c = 0; c < 32; c++) {
+                            int cc = c0 + c;
+                            if (!(__uint_as_float(r[c]) - hcs[cc] > hr)) continue;
+                            if (diag && cc <= row) continue;
+                            uint32_t idx = atomicAdd(&st->ncand, 1u);
+                            if ((int64_t)idx < L.cand_cap) {
+                                uint32_t *cd = L.cand + ((int64_t)sec * L.cand_cap + idx) * 2;
+                                cd[0] = (uint32_t)(I * TC_TILE + row);
+                                cd[1] = (uint32_t)(J * TC_TILE + cc);
+                            }
                         }
                     }
                 }
