@@ -303,6 +303,23 @@ static int bpad_for(int precision, int B)
     return ((B + 15) / 16) * 16;
 }
 
+static float f32_down(double v)
+{
+    float f = (float)v;
+    if ((double)f > v) f = std::nextafter(f, -INFINITY);
+    return f;
+}
+
+static float f32_up(double v)
+{
+    float f = (float)v;
+    if ((double)f < v) f = std::nextafter(f, INFINITY);
+    return f;
+}
+
+// Error-bound constants of the spectral screen (see warp_write_row and the
+// screen kernels): operand rounding u, eta; accumulation and evaluation
+// slack gamma; the split parameter delta of 2ab <= delta a^2 + b^2 / delta.
 static ScreenConst screen_const(const rhseg_handle *h)
 {
     ScreenConst c{};
@@ -313,23 +330,28 @@ static ScreenConst screen_const(const rhseg_handle *h)
         c.u = 0x1p-52; c.eta = 0.0; delta = 0x1p-20;
         c.gamma = (Bp + 8.0) * 0x1p-52 + 0x1p-48;
         break;
-    case 1:
-        c.u = 0x1p-11 + 0x1p-40; c.eta = 0x1p-25; delta = 0x1p-4;
-        c.gamma = 2.0 * Bp * 0x1p-23 + 0x1p-21;
+    case 1:   // FP16 operand computed in binary32: 4 binary32 roundings then RN to FP16
+        c.u = 0x1p-11 + 0x1p-20; c.eta = 0x1p-25; delta = 0x1p-4;
+        c.gamma = 2.0 * Bp * 0x1p-23 + Bp * 0x1p-24 + 0x1p-21;
         break;
     case 2:
-        c.u = 0x1p-8 + 0x1p-40; c.eta = 0x1p-133; delta = 0x1p-3;
-        c.gamma = 2.0 * Bp * 0x1p-23 + 0x1p-21;
+        c.u = 0x1p-8 + 0x1p-20; c.eta = 0x1p-133; delta = 0x1p-3;
+        c.gamma = 2.0 * Bp * 0x1p-23 + Bp * 0x1p-24 + 0x1p-21;
         break;
-    default:
-        c.u = 0x1p-24 + 0x1p-50; c.eta = 0x1p-149; delta = 0x1p-10;
-        c.gamma = Bp * 0x1p-23 + 0x1p-21;
+    default:  // binary32 operand, CUDA-core accumulation
+        c.u = 0x1p-21; c.eta = 0x1p-149; delta = 0x1p-10;
+        c.gamma = Bp * 0x1p-23 + Bp * 0x1p-24 + 0x1p-21;
         break;
     }
     double sc = (h->p.precision == 1) ? std::ldexp(1.0, -h->sigma) : 1.0;
     c.two_one_inv_delta = 2.0 * (1.0 + 1.0 / delta);
     c.kscale = (1.0 + delta) * sc * sc;
     c.xscale = sc;
+    double lam = 4.0 * (1.0 + 1.0 / delta);
+    c.Fq = f32_down(1.0 - c.gamma - lam * c.u * c.u - 0x1p-40);
+    c.E0 = f32_up(lam * c.eta * c.eta * (double)h->B);
+    c.kscale_f = f32_up(c.kscale * (1.0 + 0x1p-30));
+    c.xscale_f = (float)sc;
     return c;
 }
 

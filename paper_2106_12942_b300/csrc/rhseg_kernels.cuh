@@ -244,6 +244,11 @@ struct ScreenConst {
     double gamma;         // accumulation + evaluation slack, relative to q
     double kscale;        // (1 + delta) * 4^-sigma
     double xscale;        // 2^-sigma
+    // single-precision row terms (precision 1, 2, 3):
+    //   A = q * Fq - E0 (rounded down),  k = kscale_f / n (rounded up), with
+    //   Fq = 1 - gamma - 4 (1 + 1/delta) u^2 and E0 = 4 (1 + 1/delta) eta^2 B,
+    //   from eps^2 <= 2 u^2 q + 2 eta^2 B
+    float Fq, E0, kscale_f, xscale_f;
 };
 
 template <typename T>
@@ -254,13 +259,30 @@ template <> __device__ __forceinline__ __half to_op<__half>(double v) { return _
 template <> __device__ __forceinline__ __nv_bfloat16 to_op<__nv_bfloat16>(double v) { return __double2bfloat16(v); }
 
 template <typename T>
+__device__ __forceinline__ T to_op_f(float v);
+template <> __device__ __forceinline__ float to_op_f<float>(float v) { return v; }
+template <> __device__ __forceinline__ double to_op_f<double>(float v) { return (double)v; }
+template <> __device__ __forceinline__ __half to_op_f<__half>(float v) { return __float2half_rn(v); }
+template <> __device__ __forceinline__ __nv_bfloat16 to_op_f<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
+
+template <typename T>
+__device__ __forceinline__ float op_to_f(T v);
+template <> __device__ __forceinline__ float op_to_f<float>(float v) { return v; }
+template <> __device__ __forceinline__ float op_to_f<double>(double v) { return (float)v; }
+template <> __device__ __forceinline__ float op_to_f<__half>(__half v) { return __half2float(v); }
+template <> __device__ __forceinline__ float op_to_f<__nv_bfloat16>(__nv_bfloat16 v) { return __bfloat162float(v); }
+
+template <typename T>
 __device__ __forceinline__ double op_to_d(T v);
 template <> __device__ __forceinline__ double op_to_d<double>(double v) { return v; }
 template <> __device__ __forceinline__ double op_to_d<float>(float v) { return (double)v; }
 template <> __device__ __forceinline__ double op_to_d<__half>(__half v) { return (double)__half2float(v); }
 template <> __device__ __forceinline__ double op_to_d<__nv_bfloat16>(__nv_bfloat16 v) { return (double)__bfloat162float(v); }
 
-// Write operand row `pos` from slot `slot` (warp-cooperative); returns q.
+// Write operand row `pos` from slot `slot` (warp-cooperative).  The FP64
+// form computes in binary64; the other forms compute the row in binary32
+// (no FP64 instruction: B300's FP64 rate is low) with the extra roundings
+// counted in ScreenConst.
 template <typename T>
 __device__ void warp_write_row(const LevelDev &L, int sec, int slot, int pos, const ScreenConst &sc)
 {
@@ -270,29 +292,45 @@ __device__ void warp_write_row(const LevelDev &L, int sec, int slot, int pos, co
     int64_t n = L.n[ro + slot];
     const int32_t *ref = L.ref + (int64_t)sec * L.Bs;
     T *X = (T *)L.X + (L.poff[sec] + pos) * (int64_t)L.Bpad;
-    double rinv = 1.0 / (double)n;
-    double q = 0.0;
-    for (int b = lane; b < L.Bpad; b += 32) {
-        T v;
-        if (b < L.B) {
-            double x = (double)(S[b] - n * (int64_t)ref[b]) * rinv * sc.xscale;
-            v = to_op<T>(x);
-        } else {
-            v = to_op<T>(0.0);
+    if (sizeof(T) == 8) {
+        double rinv = 1.0 / (double)n;
+        double q = 0.0;
+        for (int b = lane; b < L.Bpad; b += 32) {
+            T v;
+            if (b < L.B) v = to_op<T>((double)(S[b] - n * (int64_t)ref[b]) * rinv * sc.xscale);
+            else v = to_op<T>(0.0);
+            X[b] = v;
+            double xd = op_to_d<T>(v);
+            q = fma(xd, xd, q);
         }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) q += __shfl_xor_sync(0xffffffffu, q, o);
+        if (lane == 0) {
+            double qq = q * (1.0 + 0x1p-40);
+            double eps = (sc.u * sqrt(qq) + sc.eta * sqrt((double)L.B)) * (1.0 + 0x1p-30);
+            double A = qq - sc.two_one_inv_delta * eps * eps - sc.gamma * qq;
+            double k = sc.kscale / (double)n * (1.0 + 0x1p-40);
+            L.Ad[L.poff[sec] + pos] = A;
+            L.kd[L.poff[sec] + pos] = k;
+        }
+        return;
+    }
+    const float nf = __ll2float_rn(n);
+    const float rinv = 1.0f / nf;
+    float q = 0.0f;
+    for (int b = lane; b < L.Bpad; b += 32) {
+        float x = 0.0f;
+        if (b < L.B) x = __ll2float_rn(S[b] - n * (int64_t)ref[b]) * rinv * sc.xscale_f;
+        T v = to_op_f<T>(x);
         X[b] = v;
-        double xd = op_to_d<T>(v);
-        q = fma(xd, xd, q);
+        float xd = op_to_f<T>(v);
+        q = fmaf(xd, xd, q);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) q += __shfl_xor_sync(0xffffffffu, q, o);
     if (lane == 0) {
-        double qq = q * (1.0 + 0x1p-40);
-        double eps = (sc.u * sqrt(qq) + sc.eta * sqrt((double)L.B)) * (1.0 + 0x1p-30);
-        double A = qq - sc.two_one_inv_delta * eps * eps - sc.gamma * qq;
-        double k = sc.kscale / (double)n * (1.0 + 0x1p-40);
-        if (L.precision == 0) { L.Ad[L.poff[sec] + pos] = A; L.kd[L.poff[sec] + pos] = k; }
-        else { L.Af[L.poff[sec] + pos] = __double2float_rd(A); L.kf[L.poff[sec] + pos] = __double2float_ru(k); }
+        L.Af[L.poff[sec] + pos] = __fmaf_rd(q, sc.Fq, -sc.E0);
+        L.kf[L.poff[sec] + pos] = __fdiv_ru(sc.kscale_f, __ll2float_rd(n));
     }
 }
 
@@ -605,7 +643,7 @@ __device__ void block_compact(const LevelDev &L, int sec, const ScreenConst &sc,
 }
 
 // Step 2 of HSEG: merge the adjacent pair of minimum key.
-__global__ void __launch_bounds__(STEP_THREADS) k_adj_step(LevelDev L, ScreenConst sc)
+__global__ void __launch_bounds__(STEP_THREADS, 1) k_adj_step(LevelDev L, ScreenConst sc)
 {
     int sec = blockIdx.x;
     if (sec >= L.nsec) return;
@@ -622,10 +660,11 @@ __global__ void __launch_bounds__(STEP_THREADS) k_adj_step(LevelDev L, ScreenCon
     if (threadIdx.x == 0) { st->iter += 1; st->pairs += st->nadj; }
     PairKey best = pk_none();
     for (int i = threadIdx.x; i < m0; i += blockDim.x) {
-        if (!L.alive[ro + i]) continue;
+        // absorbed slots carry RHSEG_KEY_NONE
         uint64_t k = L.bestK[ro + i];
+        int32_t bp = L.bestP[ro + i];
         if (k == RHSEG_KEY_NONE) continue;
-        PairKey c = pk_make(k, i, L.bestP[ro + i]);
+        PairKey c = pk_make(k, i, bp);
         if (pk_less(c, best)) best = c;
     }
     best = block_min_pk(best, sm.pk);
@@ -671,7 +710,7 @@ __global__ void __launch_bounds__(STEP_THREADS) k_adj_step(LevelDev L, ScreenCon
 // Step 3 of HSEG: exact re-check of the screen's candidates (or of every
 // non-adjacent pair when no finite threshold exists or the candidate buffer
 // overflowed), merge of the minimum if below the threshold.
-__global__ void __launch_bounds__(STEP_THREADS) k_spec_step(LevelDev L, ScreenConst sc)
+__global__ void __launch_bounds__(STEP_THREADS, 1) k_spec_step(LevelDev L, ScreenConst sc)
 {
     int sec = blockIdx.x;
     if (sec >= L.nsec) return;

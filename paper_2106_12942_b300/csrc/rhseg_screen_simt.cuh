@@ -64,14 +64,17 @@ __device__ void block_tile_prefix(const LevelDev &L, int tile, long long *pre)
     __syncthreads();
 }
 
-// Decode a local upper-triangle tile index into (I, J), I <= J < nb.
+// Decode a local upper-triangle tile index into (I, J), I <= J < nb
+// (binary32 estimate, exact integer correction; no FP64 instruction).
 __device__ __forceinline__ void tri_decode(long long local, long long nb, int &I, int &J)
 {
-    double a = 2.0 * nb + 1.0;
-    long long i = (long long)((a - sqrt(a * a - 8.0 * (double)local)) / 2.0);
+    float a = 2.0f * (float)nb + 1.0f;
+    float disc = fmaxf(a * a - 8.0f * (float)local, 0.0f);
+    long long i = (long long)((a - sqrtf(disc)) * 0.5f);
     if (i < 0) i = 0;
+    if (i > nb - 1) i = nb - 1;
     while (i > 0 && i * nb - i * (i - 1) / 2 > local) i--;
-    while ((i + 1) * nb - (i + 1) * i / 2 <= local) i++;
+    while (i + 1 < nb && (i + 1) * nb - (i + 1) * i / 2 <= local) i++;
     long long off = i * nb - i * (i - 1) / 2;
     I = (int)i;
     J = (int)(i + (local - off));

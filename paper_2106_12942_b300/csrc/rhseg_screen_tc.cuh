@@ -192,6 +192,21 @@ __device__ __forceinline__ bool tc_tile(const LevelDev &L, const TcJob &job, con
     return true;
 }
 
+// tc_tile computed by lane 0 and broadcast to the warp.
+__device__ __forceinline__ bool tc_tile_warp(const LevelDev &L, const TcJob &job, const long long *pre, long long t,
+                                             long long total, int &sec, int &I, int &J, int64_t &rowA, int64_t &rowB)
+{
+    int have = 0;
+    if ((threadIdx.x & 31) == 0) have = tc_tile(L, job, pre, t, total, sec, I, J, rowA, rowB) ? 1 : 0;
+    have = __shfl_sync(0xffffffffu, have, 0);
+    sec = __shfl_sync(0xffffffffu, sec, 0);
+    I = __shfl_sync(0xffffffffu, I, 0);
+    J = __shfl_sync(0xffffffffu, J, 0);
+    rowA = __shfl_sync(0xffffffffu, rowA, 0);
+    rowB = __shfl_sync(0xffffffffu, rowB, 0);
+    return have != 0;
+}
+
 template <int FMT>
 __global__ void __launch_bounds__(TC_THREADS, 1) k_screen_tc(LevelDev L, const __grid_constant__ CUtensorMap tmap,
                                                              TcJob job)
@@ -298,26 +313,26 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_screen_tc(LevelDev L, const _
         int tcount = 0;
         float hc_next = inf, hr_next = inf;
         {
-            int sec, I, J;
-            int64_t rowA, rowB;
-            if (job.gram_rows == 0 && tc_tile(L, job, sh.pre, blockIdx.x, total, sec, I, J, rowA, rowB)) {
+            int sec = 0, I = 0, J = 0;
+            int64_t rowA = 0, rowB = 0;
+            if (tc_tile_warp(L, job, sh.pre, blockIdx.x, total, sec, I, J, rowA, rowB) && job.gram_rows == 0) {
                 hc_next = L.H[rowB + et];
                 hr_next = L.H[rowA + row];
             }
         }
         for (long long t = blockIdx.x;; t += gridDim.x, tcount++) {
             int sec = 0, I = 0, J = 0;
-            int64_t rowA, rowB;
-            bool have = tc_tile(L, job, sh.pre, t, total, sec, I, J, rowA, rowB);
+            int64_t rowA = 0, rowB = 0;
+            bool have = tc_tile_warp(L, job, sh.pre, t, total, sec, I, J, rowA, rowB);
             if (epi_bar_or(!have || *abort)) break;          // uniform over the 128 threads
             const int buf = tcount & 1;
             sh.hc[buf][et] = hc_next;
             const float hr = hr_next;
             asm volatile("bar.sync 1, 128;" ::: "memory");
             if (job.gram_rows == 0) {
-                int s2, I2, J2;
-                int64_t rA2, rB2;
-                if (tc_tile(L, job, sh.pre, t + gridDim.x, total, s2, I2, J2, rA2, rB2)) {
+                int s2 = 0, I2 = 0, J2 = 0;
+                int64_t rA2 = 0, rB2 = 0;
+                if (tc_tile_warp(L, job, sh.pre, t + gridDim.x, total, s2, I2, J2, rA2, rB2)) {
                     hc_next = L.H[rB2 + et];
                     hr_next = L.H[rA2 + row];
                 }
