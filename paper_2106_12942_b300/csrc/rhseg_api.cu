@@ -610,7 +610,7 @@ static void launch_screen(rhseg_handle *h, const LevelDev &L)
     case 3: k_screen_simt<float, float><<<grid, 256, 0, h->stream>>>(L); break;
     default: {
         TcJob job{0, nullptr};
-        cudaError_t e = launch_screen_tc_map(L, h->tmap, h->p.precision, h->n_sm * 2, h->stream, job);
+        cudaError_t e = launch_screen_tc_map(L, h->tmap, h->p.precision, h->n_sm, h->stream, job);
         if (e != cudaSuccess) h->launch_err = e;
         break;
     }
@@ -1191,7 +1191,12 @@ extern "C" int rhseg_gram_tc(const void *X, int32_t rows, int32_t Bpad, int32_t 
     L.nsec = 1;
     TcJob job{rows, G};
     int nb = rows / TC_TILE;
-    CK(launch_screen_tc_map(L, map, precision, std::min(nb * nb, 296), (cudaStream_t)cuda_stream, job));
+    int nsm = 148;
+    {
+        int dev = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    }
+    CK(launch_screen_tc_map(L, map, precision, std::min(nb * nb, nsm), (cudaStream_t)cuda_stream, job));
     return RHSEG_OK;
 }
 

@@ -16,7 +16,7 @@
 
 namespace rhseg {
 
-constexpr int STEP_THREADS = 512;
+constexpr int STEP_THREADS = 256;     // two step blocks per SM: every section of a level in one wave
 constexpr int NB_CHUNK_WORDS = 64;      // adjacency words gathered per chunk
 constexpr int RESCAN_CAP = 512;
 
@@ -643,7 +643,7 @@ __device__ void block_compact(const LevelDev &L, int sec, const ScreenConst &sc,
 }
 
 // Step 2 of HSEG: merge the adjacent pair of minimum key.
-__global__ void __launch_bounds__(STEP_THREADS, 1) k_adj_step(LevelDev L, ScreenConst sc)
+__global__ void __launch_bounds__(STEP_THREADS, 2) k_adj_step(LevelDev L, ScreenConst sc)
 {
     int sec = blockIdx.x;
     if (sec >= L.nsec) return;
@@ -710,7 +710,7 @@ __global__ void __launch_bounds__(STEP_THREADS, 1) k_adj_step(LevelDev L, Screen
 // Step 3 of HSEG: exact re-check of the screen's candidates (or of every
 // non-adjacent pair when no finite threshold exists or the candidate buffer
 // overflowed), merge of the minimum if below the threshold.
-__global__ void __launch_bounds__(STEP_THREADS, 1) k_spec_step(LevelDev L, ScreenConst sc)
+__global__ void __launch_bounds__(STEP_THREADS, 2) k_spec_step(LevelDev L, ScreenConst sc)
 {
     int sec = blockIdx.x;
     if (sec >= L.nsec) return;

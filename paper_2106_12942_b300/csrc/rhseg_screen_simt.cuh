@@ -68,8 +68,8 @@ __device__ void block_tile_prefix(const LevelDev &L, int tile, long long *pre)
 // (binary32 estimate, exact integer correction; no FP64 instruction).
 __device__ __forceinline__ void tri_decode(long long local, long long nb, int &I, int &J)
 {
-    float a = 2.0f * (float)nb + 1.0f;
-    float disc = fmaxf(a * a - 8.0f * (float)local, 0.0f);
+    float a = 2.0f * (float)(int)nb + 1.0f;                 // 32-bit conversions only
+    float disc = fmaxf(a * a - 8.0f * (float)(int)local, 0.0f);
     long long i = (long long)((a - sqrtf(disc)) * 0.5f);
     if (i < 0) i = 0;
     if (i > nb - 1) i = nb - 1;

@@ -100,12 +100,23 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volati
     return true;
 }
 
-__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y, uint64_t *bar)
+// L2 policy for the streamed operand rows: evicted before other lines, so
+// that the streaming does not push the region tables of the step kernels
+// out of L2 between iterations.
+__device__ __forceinline__ uint64_t l2_evict_first_policy()
+{
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y, uint64_t *bar,
+                                            uint64_t policy)
 {
     asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
-            smem_u32(dst)),
-        "l"((uint64_t)map), "r"(x), "r"(y), "r"(smem_u32(bar))
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1, {%2, "
+        "%3}], [%4], %5;" ::"r"(smem_u32(dst)),
+        "l"((uint64_t)map), "r"(x), "r"(y), "r"(smem_u32(bar)), "l"(policy)
         : "memory");
 }
 
@@ -251,6 +262,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_screen_tc(LevelDev L, const _
         if (lane == 0) {
             int stage = 0;
             uint32_t phase = 0;
+            const uint64_t pol = l2_evict_first_policy();
             for (long long t = blockIdx.x; !*abort; t += gridDim.x) {
                 int sec, I, J;
                 int64_t rowA, rowB;
@@ -260,8 +272,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_screen_tc(LevelDev L, const _
                     uint8_t *a = ring + stage * TC_STAGE_BYTES;
                     uint8_t *b = a + TC_TILE * TC_KATOM * 2;
                     mbar_expect_tx(&sh.full[stage], TC_STAGE_BYTES);
-                    tma_load_2d(a, &tmap, kc * TC_KATOM, (int)rowA, &sh.full[stage]);
-                    tma_load_2d(b, &tmap, kc * TC_KATOM, (int)rowB, &sh.full[stage]);
+                    tma_load_2d(a, &tmap, kc * TC_KATOM, (int)rowA, &sh.full[stage], pol);
+                    tma_load_2d(b, &tmap, kc * TC_KATOM, (int)rowB, &sh.full[stage], pol);
                     if (++stage == TC_STAGES) { stage = 0; phase ^= 1; }
                 }
             }
@@ -388,6 +400,233 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_screen_tc(LevelDev L, const _
 }
 
 // ---------------------------------------------------------------------------
+// Resident-A variant (Bpad <= 256): each persistent CTA walks a contiguous
+// range of the tile list (row-major upper triangle per section), so
+// consecutive tiles share the 128-row block I.  That block (all K) stays in
+// shared memory (two buffers: the next row block loads while the current one
+// is in use) and only the J blocks stream through a 4-stage ring, which
+// halves the L2 traffic per MMA compared with loading both operands per
+// tile.  Roles, accumulators, epilogue and bounded waits are as above.
+// ---------------------------------------------------------------------------
+
+constexpr int RA_STAGES = 4;
+constexpr int RA_ATOM_BYTES = TC_TILE * TC_KATOM * 2;      // 16 KB: 128 rows x 64 fp16
+constexpr int RA_NK_MAX = 4;                                // Bpad <= 256
+struct RaShared {
+    uint64_t bfull[RA_STAGES], bempty[RA_STAGES];
+    uint64_t afull[2], afree[2];
+    uint64_t tfull[2], tempty[2];
+    uint32_t tmem_base;
+    int abort;
+    alignas(16) float hc[2][TC_TILE];
+    long long pre[MAX_SECTIONS + 1];
+};
+constexpr int RA_SMEM_BYTES =
+    (2 * RA_NK_MAX + RA_STAGES) * RA_ATOM_BYTES + 1024 + (int)((sizeof(RaShared) + 127) / 128 * 128);
+
+template <int FMT>
+__global__ void __launch_bounds__(TC_THREADS, 1) k_screen_tc_ra(LevelDev L, const __grid_constant__ CUtensorMap tmap,
+                                                                TcJob job)
+{
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    uint8_t *abuf = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);   // [2][RA_NK_MAX] atoms
+    uint8_t *ring = abuf + 2 * RA_NK_MAX * RA_ATOM_BYTES;                              // [RA_STAGES] atoms
+    RaShared &sh = *(RaShared *)(ring + RA_STAGES * RA_ATOM_BYTES);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nk = L.Bpad / TC_KATOM;
+
+    long long total;
+    if (job.gram_rows > 0) {
+        long long nb = job.gram_rows / TC_TILE;
+        total = nb * nb;
+    } else {
+        block_tile_prefix(L, TC_TILE, sh.pre);
+        total = sh.pre[L.nsec];
+    }
+    const long long t0 = total * blockIdx.x / gridDim.x;
+    const long long t1 = total * (blockIdx.x + 1) / gridDim.x;
+    if (t0 >= t1) return;     // uniform: this CTA has no tile
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < RA_STAGES; s++) { mbar_init(&sh.bfull[s], 1); mbar_init(&sh.bempty[s], 1); }
+        for (int b = 0; b < 2; b++) {
+            mbar_init(&sh.afull[b], 1); mbar_init(&sh.afree[b], 1);
+            mbar_init(&sh.tfull[b], 1); mbar_init(&sh.tempty[b], 4 * 32);
+        }
+        sh.abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&sh.tmem_base)),
+                     "r"(256)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tbase = sh.tmem_base;
+    volatile int *abort = &sh.abort;
+
+    if (warp == 0) {
+        // ---------------- TMA producer ----------------
+        if (lane == 0) {
+            const uint64_t pol = l2_evict_first_policy();
+            int stage = 0, ab = 1;
+            uint32_t phase = 0;
+            uint32_t aload[2] = {0, 0};
+            int64_t prevA = -1;
+            for (long long t = t0; t < t1 && !*abort; t++) {
+                int sec, I, J;
+                int64_t rowA, rowB;
+                tc_tile(L, job, sh.pre, t, total, sec, I, J, rowA, rowB);
+                if (rowA != prevA) {
+                    ab ^= 1;
+                    if (!mbar_wait(&sh.afree[ab], (aload[ab] & 1) ^ 1, abort, L.err)) break;
+                    mbar_expect_tx(&sh.afull[ab], (uint32_t)(nk * RA_ATOM_BYTES));
+                    for (int k = 0; k < nk; k++)
+                        tma_load_2d(abuf + (ab * RA_NK_MAX + k) * RA_ATOM_BYTES, &tmap, k * TC_KATOM, (int)rowA,
+                                    &sh.afull[ab], pol);
+                    aload[ab]++;
+                    prevA = rowA;
+                }
+                bool ok = true;
+                for (int k = 0; k < nk; k++) {
+                    if (!mbar_wait(&sh.bempty[stage], phase ^ 1, abort, L.err)) { ok = false; break; }
+                    mbar_expect_tx(&sh.bfull[stage], RA_ATOM_BYTES);
+                    tma_load_2d(ring + stage * RA_ATOM_BYTES, &tmap, k * TC_KATOM, (int)rowB, &sh.bfull[stage], pol);
+                    if (++stage == RA_STAGES) { stage = 0; phase ^= 1; }
+                }
+                if (!ok) break;
+            }
+        }
+        __syncwarp();
+    } else if (warp == 1) {
+        // ---------------- MMA issuer ----------------
+        if (lane == 0) {
+            const uint32_t idesc = idesc_f16(FMT);
+            int stage = 0, ab = 1, tcount = 0;
+            uint32_t phase = 0;
+            uint32_t ause[2] = {0, 0};
+            int64_t prevA = -1;
+            for (long long t = t0; t < t1 && !*abort; t++, tcount++) {
+                int sec, I, J;
+                int64_t rowA, rowB;
+                tc_tile(L, job, sh.pre, t, total, sec, I, J, rowA, rowB);
+                if (rowA != prevA) {
+                    if (prevA >= 0) tc_commit(&sh.afree[ab]);      // previous row block free once its MMAs end
+                    ab ^= 1;
+                    if (!mbar_wait(&sh.afull[ab], ause[ab] & 1, abort, L.err)) break;
+                    ause[ab]++;
+                    prevA = rowA;
+                }
+                const int buf = tcount & 1;
+                if (!mbar_wait(&sh.tempty[buf], ((tcount >> 1) & 1) ^ 1, abort, L.err)) break;
+                tc_fence_after();
+                const uint32_t dt = tbase + (uint32_t)(buf * TC_TILE);
+                const uint32_t abase = smem_u32(abuf + ab * RA_NK_MAX * RA_ATOM_BYTES);
+                bool ok = true;
+                for (int k = 0; k < nk; k++) {
+                    if (!mbar_wait(&sh.bfull[stage], phase, abort, L.err)) { ok = false; break; }
+                    tc_fence_after();
+                    const uint64_t ad = sdesc_sw128(abase + k * RA_ATOM_BYTES);
+                    const uint64_t bd = sdesc_sw128(smem_u32(ring + stage * RA_ATOM_BYTES));
+#pragma unroll
+                    for (int kk = 0; kk < TC_KATOM / 16; kk++)
+                        tc_mma(dt, ad + (uint64_t)(2 * kk), bd + (uint64_t)(2 * kk), idesc, (k > 0 || kk > 0) ? 1u : 0u);
+                    tc_commit(&sh.bempty[stage]);
+                    if (++stage == RA_STAGES) { stage = 0; phase ^= 1; }
+                }
+                if (!ok) break;
+                tc_commit(&sh.tfull[buf]);
+            }
+        }
+        __syncwarp();
+    } else {
+        // ---------------- epilogue: warps 2..5 ----------------
+        const int q = warp & 3;
+        const int row = q * 32 + lane;
+        const int et = threadIdx.x - 64;
+        const float inf = __int_as_float(0x7f800000);
+        int tcount = 0;
+        float hc_next = inf, hr_next = inf;
+        {
+            int sec = 0, I = 0, J = 0;
+            int64_t rowA = 0, rowB = 0;
+            if (tc_tile_warp(L, job, sh.pre, t0, total, sec, I, J, rowA, rowB) && job.gram_rows == 0) {
+                hc_next = L.H[rowB + et];
+                hr_next = L.H[rowA + row];
+            }
+        }
+        for (long long t = t0;; t++, tcount++) {
+            int sec = 0, I = 0, J = 0;
+            int64_t rowA = 0, rowB = 0;
+            bool have = (t < t1) && tc_tile_warp(L, job, sh.pre, t, total, sec, I, J, rowA, rowB);
+            if (epi_bar_or(!have || *abort)) break;
+            const int buf = tcount & 1;
+            sh.hc[buf][et] = hc_next;
+            const float hr = hr_next;
+            asm volatile("bar.sync 1, 128;" ::: "memory");
+            if (job.gram_rows == 0 && t + 1 < t1) {
+                int s2 = 0, I2 = 0, J2 = 0;
+                int64_t rA2 = 0, rB2 = 0;
+                if (tc_tile_warp(L, job, sh.pre, t + 1, total, s2, I2, J2, rA2, rB2)) {
+                    hc_next = L.H[rB2 + et];
+                    hr_next = L.H[rA2 + row];
+                }
+            }
+            bool ok = mbar_wait(&sh.tfull[buf], (tcount >> 1) & 1, abort, L.err);
+            ok = __all_sync(0xffffffffu, ok);
+            if (!ok) continue;
+            tc_fence_after();
+            const uint32_t taddr = tbase + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * TC_TILE);
+            if (job.gram_rows > 0) {
+                for (int c0 = 0; c0 < TC_TILE; c0 += 32) {
+                    uint32_t r[32];
+                    tmem_ld32(taddr + (uint32_t)c0, r);
+                    float *o = job.gram_out + ((int64_t)I * TC_TILE + row) * job.gram_rows + (int64_t)J * TC_TILE + c0;
+#pragma unroll
+                    for (int c = 0; c < 32; c++) o[c] = __uint_as_float(r[c]);
+                }
+            } else {
+                SecState *st = &L.st[sec];
+                const bool diag = (I == J);
+                const float *hcs = sh.hc[buf];
+                for (int c0 = 0; c0 < TC_TILE; c0 += 32) {
+                    uint32_t r[32];
+                    tmem_ld32(taddr + (uint32_t)c0, r);
+                    float m = -inf;
+#pragma unroll
+                    for (int c = 0; c < 32; c++) m = fmaxf(m, __uint_as_float(r[c]) - hcs[c0 + c]);
+                    if (m > hr) {
+                        for (int c = 0; c < 32; c++) {
+                            int cc = c0 + c;
+                            if (!(__uint_as_float(r[c]) - hcs[cc] > hr)) continue;
+                            if (diag && cc <= row) continue;
+                            uint32_t idx = atomicAdd(&st->ncand, 1u);
+                            if ((int64_t)idx < L.cand_cap) {
+                                uint32_t *cd = L.cand + ((int64_t)sec * L.cand_cap + idx) * 2;
+                                cd[0] = (uint32_t)(I * TC_TILE + row);
+                                cd[1] = (uint32_t)(J * TC_TILE + cc);
+                            }
+                        }
+                    }
+                }
+            }
+            tc_fence_before();
+            mbar_arrive(&sh.tempty[buf]);
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(256) : "memory");
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Host side: tensor map over the operand rows and the launch.
 // ---------------------------------------------------------------------------
 
@@ -429,22 +668,33 @@ inline int make_operand_map(CUtensorMap *map, const void *X, int64_t rows, int B
 inline bool screen_uses_tcgen05(int precision) { return precision == 1 || precision == 2; }
 
 // Launch the screen for a level.  `map` must describe L.X.
-inline cudaError_t launch_screen_tc_map(const LevelDev &L, const CUtensorMap &map, int precision, int grid,
+inline cudaError_t launch_screen_tc_map(const LevelDev &L, const CUtensorMap &map, int precision, int n_sm,
                                         cudaStream_t s, TcJob job)
 {
-    static bool attr_done[2] = {false, false};
-    int fi = precision == 2 ? 1 : 0;
+    static bool attr_done[4] = {false, false, false, false};
+    const bool ra = L.Bpad <= RA_NK_MAX * TC_KATOM;
+    int fi = (precision == 2 ? 1 : 0) + (ra ? 2 : 0);
     if (!attr_done[fi]) {
-        cudaError_t e = (precision == 2)
-                            ? cudaFuncSetAttribute(k_screen_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                   TC_SMEM_BYTES)
-                            : cudaFuncSetAttribute(k_screen_tc<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                   TC_SMEM_BYTES);
+        cudaError_t e;
+        if (ra)
+            e = (precision == 2)
+                    ? cudaFuncSetAttribute(k_screen_tc_ra<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, RA_SMEM_BYTES)
+                    : cudaFuncSetAttribute(k_screen_tc_ra<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, RA_SMEM_BYTES);
+        else
+            e = (precision == 2)
+                    ? cudaFuncSetAttribute(k_screen_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM_BYTES)
+                    : cudaFuncSetAttribute(k_screen_tc<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM_BYTES);
         if (e != cudaSuccess) return e;
         attr_done[fi] = true;
     }
-    if (precision == 2) k_screen_tc<1><<<grid, TC_THREADS, TC_SMEM_BYTES, s>>>(L, map, job);
-    else k_screen_tc<0><<<grid, TC_THREADS, TC_SMEM_BYTES, s>>>(L, map, job);
+    if (ra) {
+        // one CTA per SM; each walks a contiguous range of tiles
+        if (precision == 2) k_screen_tc_ra<1><<<n_sm, TC_THREADS, RA_SMEM_BYTES, s>>>(L, map, job);
+        else k_screen_tc_ra<0><<<n_sm, TC_THREADS, RA_SMEM_BYTES, s>>>(L, map, job);
+    } else {
+        if (precision == 2) k_screen_tc<1><<<2 * n_sm, TC_THREADS, TC_SMEM_BYTES, s>>>(L, map, job);
+        else k_screen_tc<0><<<2 * n_sm, TC_THREADS, TC_SMEM_BYTES, s>>>(L, map, job);
+    }
     return cudaGetLastError();
 }
 
