@@ -265,6 +265,8 @@ def main():
         "kernel_ms": {"screen": scr_ms / args.steps, "adj_step": sum(s["adj_ms"] for s in stats) / args.steps,
                       "spec_step": sum(s["spec_ms"] for s in stats) / args.steps},
         "screen": {"screened_pairs": stats[-1]["screened_pairs"], "candidates": stats[-1]["candidates"],
+                   "candidate_fraction": stats[-1]["candidates"] / max(1, stats[-1]["screened_pairs"]),
+                   "candidates_below_threshold": stats[-1]["candidates_below"],
                    "fallbacks": stats[-1]["fallbacks"]},
         "level_ms": [round(x, 2) for x in stats[-1]["level_ms"][:params["rnb_levels"]]],
         "level_iters": stats[-1]["level_iters"][:params["rnb_levels"]],

@@ -109,6 +109,8 @@ typedef struct rhseg_stats {
     int32_t stalled_sections, n_levels_out;
     double  run_ms;           /* device time of the last rhseg_run                */
     int64_t kernel_launches;  /* kernels launched by the last rhseg_run            */
+    int64_t candidates_below; /* candidates that were non-adjacent with exact K below
+                                 the threshold (the rest were screen false positives) */
     int64_t screen_launches;  /* spectral-screen launches                          */
     double  screen_ms, adj_ms, spec_ms;  /* summed device time per step kernel
                                             (profile = 1 only, else 0)            */

@@ -39,7 +39,7 @@ class Stats(C.Structure):
         ("screened_pairs", C.c_int64), ("candidates", C.c_int64), ("fallbacks", C.c_int64),
         ("stalled_sections", C.c_int32), ("n_levels_out", C.c_int32),
         ("run_ms", C.c_double),
-        ("kernel_launches", C.c_int64), ("screen_launches", C.c_int64),
+        ("kernel_launches", C.c_int64), ("candidates_below", C.c_int64), ("screen_launches", C.c_int64),
         ("screen_ms", C.c_double), ("adj_ms", C.c_double), ("spec_ms", C.c_double),
         ("screen_impl", C.c_int32), ("pad", C.c_int32),
         ("level_ms", C.c_double * 6), ("level_iters", C.c_int32 * 6),

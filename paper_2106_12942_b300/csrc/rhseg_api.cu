@@ -805,6 +805,7 @@ static int run_impl(rhseg_handle *h)
             h->stats.iterations += q.iter;
             h->stats.screened_pairs += q.screened;
             h->stats.candidates += q.cands;
+            h->stats.candidates_below += q.cands_true;
             h->stats.fallbacks += q.fallbacks;
             h->stats.stalled_sections += q.stalled;
             h->stats.merges_adj += q.madj;

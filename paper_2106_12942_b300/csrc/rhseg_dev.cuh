@@ -29,6 +29,7 @@ struct SecState {
     int64_t pairs;         // dissimilarities the method defines, accumulated
     int64_t screened;      // pairs evaluated by the screen
     int64_t cands;         // candidates passed to the exact re-check
+    int64_t cands_true;    // of those, non-adjacent pairs with exact K below the threshold
     int64_t fallbacks;     // spectral steps resolved exhaustively
     int64_t log_n;         // records written in this section's log segment
     uint32_t ncand;        // candidates emitted in the current step

@@ -315,12 +315,17 @@ __device__ void warp_write_row(const LevelDev &L, int sec, int slot, int pos, co
         }
         return;
     }
-    const float nf = __ll2float_rn(n);
+    const float nf = __int2float_rn((int)n);                 // n < 2^31 (pixels of the image)
     const float rinv = 1.0f / nf;
     float q = 0.0f;
     for (int b = lane; b < L.Bpad; b += 32) {
         float x = 0.0f;
-        if (b < L.B) x = __ll2float_rn(S[b] - n * (int64_t)ref[b]) * rinv * sc.xscale_f;
+        if (b < L.B) {
+            // |S - n ref| < 2^55: two exact 32-bit halves, one rounding in the fma
+            int64_t v = S[b] - n * (int64_t)ref[b];
+            float xv = fmaf(__int2float_rn((int)(v >> 24)), 16777216.0f, __int2float_rn((int)(v & 0xFFFFFF)));
+            x = xv * rinv * sc.xscale_f;
+        }
         T v = to_op_f<T>(x);
         X[b] = v;
         float xd = op_to_f<T>(v);
@@ -330,7 +335,7 @@ __device__ void warp_write_row(const LevelDev &L, int sec, int slot, int pos, co
     for (int o = 16; o > 0; o >>= 1) q += __shfl_xor_sync(0xffffffffu, q, o);
     if (lane == 0) {
         L.Af[L.poff[sec] + pos] = __fmaf_rd(q, sc.Fq, -sc.E0);
-        L.kf[L.poff[sec] + pos] = __fdiv_ru(sc.kscale_f, __ll2float_rd(n));
+        L.kf[L.poff[sec] + pos] = __fdiv_ru(sc.kscale_f, __int2float_rd((int)n));
     }
 }
 
@@ -739,6 +744,7 @@ __global__ void __launch_bounds__(STEP_THREADS, 2) k_spec_step(LevelDev L, Scree
             if ((A[(int64_t)i * W + (j >> 5)] >> (j & 31)) & 1) continue;
             double K = warp_key(L.S + (ro + i) * L.Bs, L.n[ro + i], L.S + (ro + j) * L.Bs, L.n[ro + j], L.B, L.err);
             if (!(K < t)) continue;
+            if ((threadIdx.x & 31) == 0) atomicAdd((unsigned long long *)&st->cands_true, 1ull);
             PairKey pc = pk_make(dbits(K), i, j);
             if (pk_less(pc, best)) best = pc;
         }

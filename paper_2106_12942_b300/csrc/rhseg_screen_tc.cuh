@@ -400,9 +400,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_screen_tc(LevelDev L, const _
 }
 
 // ---------------------------------------------------------------------------
-// Resident-A variant (Bpad <= 256): each persistent CTA walks a contiguous
-// range of the tile list (row-major upper triangle per section), so
-// consecutive tiles share the 128-row block I.  That block (all K) stays in
+// Resident-A variant (Bpad <= 256): each persistent CTA walks chunks of
+// consecutive tiles of the tile list (row-major upper triangle per section),
+// so consecutive tiles mostly share the 128-row block I.  That block (all K) stays in
 // shared memory (two buffers: the next row block loads while the current one
 // is in use) and only the J blocks stream through a 4-stage ring, which
 // halves the L2 traffic per MMA compared with loading both operands per
@@ -424,6 +424,25 @@ struct RaShared {
 constexpr int RA_SMEM_BYTES =
     (2 * RA_NK_MAX + RA_STAGES) * RA_ATOM_BYTES + 1024 + (int)((sizeof(RaShared) + 127) / 128 * 128);
 
+// Tile walk of a resident-A CTA: chunks of RA_CHUNK consecutive tiles (mostly
+// one row block, so the A operand is reused), chunks dealt round-robin to the
+// CTAs so that the tiles in flight at any time stay close together (their
+// operand rows are shared through L2).
+constexpr int RA_CHUNK = 16;
+
+__device__ __forceinline__ long long ra_first(long long total)
+{
+    long long t = (long long)blockIdx.x * RA_CHUNK;
+    return t < total ? t : -1;
+}
+
+__device__ __forceinline__ long long ra_next(long long t, long long total)
+{
+    long long nt = t + 1;
+    if (nt % RA_CHUNK == 0) nt = (t / RA_CHUNK + gridDim.x) * RA_CHUNK;
+    return nt < total ? nt : -1;
+}
+
 template <int FMT>
 __global__ void __launch_bounds__(TC_THREADS, 1) k_screen_tc_ra(LevelDev L, const __grid_constant__ CUtensorMap tmap,
                                                                 TcJob job)
@@ -443,9 +462,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_screen_tc_ra(LevelDev L, cons
         block_tile_prefix(L, TC_TILE, sh.pre);
         total = sh.pre[L.nsec];
     }
-    const long long t0 = total * blockIdx.x / gridDim.x;
-    const long long t1 = total * (blockIdx.x + 1) / gridDim.x;
-    if (t0 >= t1) return;     // uniform: this CTA has no tile
+    const long long t0 = ra_first(total);
+    if (t0 < 0) return;       // uniform: this CTA has no tile
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < RA_STAGES; s++) { mbar_init(&sh.bfull[s], 1); mbar_init(&sh.bempty[s], 1); }
@@ -477,7 +495,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_screen_tc_ra(LevelDev L, cons
             uint32_t phase = 0;
             uint32_t aload[2] = {0, 0};
             int64_t prevA = -1;
-            for (long long t = t0; t < t1 && !*abort; t++) {
+            for (long long t = t0; t >= 0 && !*abort; t = ra_next(t, total)) {
                 int sec, I, J;
                 int64_t rowA, rowB;
                 tc_tile(L, job, sh.pre, t, total, sec, I, J, rowA, rowB);
@@ -510,7 +528,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_screen_tc_ra(LevelDev L, cons
             uint32_t phase = 0;
             uint32_t ause[2] = {0, 0};
             int64_t prevA = -1;
-            for (long long t = t0; t < t1 && !*abort; t++, tcount++) {
+            for (long long t = t0; t >= 0 && !*abort; t = ra_next(t, total), tcount++) {
                 int sec, I, J;
                 int64_t rowA, rowB;
                 tc_tile(L, job, sh.pre, t, total, sec, I, J, rowA, rowB);
@@ -559,19 +577,20 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_screen_tc_ra(LevelDev L, cons
                 hr_next = L.H[rowA + row];
             }
         }
-        for (long long t = t0;; t++, tcount++) {
+        for (long long t = t0;; t = (t >= 0 ? ra_next(t, total) : -1), tcount++) {
             int sec = 0, I = 0, J = 0;
             int64_t rowA = 0, rowB = 0;
-            bool have = (t < t1) && tc_tile_warp(L, job, sh.pre, t, total, sec, I, J, rowA, rowB);
+            bool have = (t >= 0) && tc_tile_warp(L, job, sh.pre, t, total, sec, I, J, rowA, rowB);
             if (epi_bar_or(!have || *abort)) break;
             const int buf = tcount & 1;
             sh.hc[buf][et] = hc_next;
             const float hr = hr_next;
             asm volatile("bar.sync 1, 128;" ::: "memory");
-            if (job.gram_rows == 0 && t + 1 < t1) {
+            const long long tn = ra_next(t, total);
+            if (job.gram_rows == 0 && tn >= 0) {
                 int s2 = 0, I2 = 0, J2 = 0;
                 int64_t rA2 = 0, rB2 = 0;
-                if (tc_tile_warp(L, job, sh.pre, t + 1, total, s2, I2, J2, rA2, rB2)) {
+                if (tc_tile_warp(L, job, sh.pre, tn, total, s2, I2, J2, rA2, rB2)) {
                     hc_next = L.H[rB2 + et];
                     hr_next = L.H[rA2 + row];
                 }

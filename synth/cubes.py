@@ -135,13 +135,14 @@ def make(w: Workload | int, seed: int | None = None, rows: int | None = None, co
         spectra = _class_spectra(rng, w.n_classes, w.bands)
         cls = np.arange(n_seeds) % w.n_classes
     cell = voronoi(R, Cc, seeds, angle, stretch)
-    base = spectra[cls[cell]].astype(np.float32)          # [R, C, B]
+    spectra32 = spectra.astype(np.float32)
     img = np.empty((R, Cc, w.bands), dtype=np.uint16)
     blk = max(1, (1 << 22) // max(1, Cc * w.bands))
     for r0 in range(0, R, blk):
         r1 = min(R, r0 + blk)
+        base = spectra32[cls[cell[r0:r1]]]                 # [rows of the block, C, B]
         noise = rng.standard_normal((r1 - r0, Cc, w.bands), dtype=np.float32) * np.float32(w.sigma)
-        v = np.rint(base[r0:r1] + noise)
+        v = np.rint(base + noise)
         img[r0:r1] = np.clip(v, 0, w.clip_max).astype(np.uint16)
     mask = None
     if w.mask_p > 0:

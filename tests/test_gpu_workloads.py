@@ -84,3 +84,37 @@ def test_rhseg_1024x1024x224_sampled(P, orc, cfg4):
     mg = log[log["kind"] != 2]
     assert np.all(mg["survivor_id"] < mg["absorbed_id"])
     assert np.array_equal(log["dissim"], np.sqrt(log["key"]))
+
+
+def test_rhseg_2048x2048x128_sampled(P, orc):
+    # anisotropic cells, L=6 (1024 deepest sections), w=0.5, 8 output levels
+    img, mask = synth.make(5)
+    kw = dict(synth.WORKLOADS[5].params)
+    seg = P.RHSEG(img, mask, **kw)
+    seg.run()
+    log = seg.log()
+    L = kw["rnb_levels"]
+    okw = {k: v for k, v in kw.items() if k != "precision"}
+    for s in (0, 517, 1023):
+        ref = orc.hseg_leaf(img, mask, s, max_iters=120, **okw)
+        part = log[(log["level"] == L) & (log["section"] == s)][:len(ref.log)]
+        assert len(ref.log) > 0
+        for f in ["step", "kind", "survivor_id", "absorbed_id", "nregions_after"]:
+            assert np.array_equal(part[f], ref.log[f]), (s, f)
+        assert np.array_equal(part["key"].view(np.uint64), ref.log["key"].view(np.uint64)), s
+    n = seg.n_levels()
+    assert n == kw["n_out_levels"] or seg.stats()["stalled_sections"] > 0
+    tot = img.reshape(-1, img.shape[2]).astype(np.int64).sum(0)
+    prev = None
+    for k in range(n):
+        lab, sums, cnt = seg.level(k)
+        R = len(cnt)
+        assert lab.min() >= 1 and lab.max() == R
+        assert np.array_equal(np.bincount(lab.ravel(), minlength=R + 1)[1:], cnt)
+        assert np.array_equal(sums.sum(0), tot)
+        if prev is not None:                       # coarser levels are unions of finer regions
+            pairs = np.unique(np.stack([prev.ravel(), lab.ravel()], 1), axis=0)
+            assert len(np.unique(pairs[:, 0])) == len(pairs)
+        prev = lab
+    assert len(cnt) == kw["conv_nregions"] or seg.stats()["stalled_sections"] > 0
+    seg.close()
