@@ -270,6 +270,8 @@ def main():
                    "fallbacks": stats[-1]["fallbacks"]},
         "level_ms": [round(x, 2) for x in stats[-1]["level_ms"][:params["rnb_levels"]]],
         "level_iters": stats[-1]["level_iters"][:params["rnb_levels"]],
+        "level_kernel_ms": {k: [round(x, 1) for x in stats[-1]["level_" + k + "_ms"][:params["rnb_levels"]]]
+                            for k in ("screen", "adj", "spec")},
     }
 
     if not args.no_e2e:

@@ -121,6 +121,9 @@ typedef struct rhseg_stats {
                                  level-1), set-up and HSEG iterations             */
     int32_t level_iters[6];   /* HSEG iterations run at each level (max over
                                  its sections)                                    */
+    double  level_screen_ms[6], level_adj_ms[6], level_spec_ms[6];
+                              /* per level split of screen_ms, adj_ms, spec_ms
+                                 (profile = 1 only)                               */
 } rhseg_stats;
 
 typedef struct rhseg_handle rhseg_handle;

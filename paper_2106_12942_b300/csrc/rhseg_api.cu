@@ -780,11 +780,14 @@ static int run_impl(rhseg_handle *h)
                     float a = 0, b = 0, c = 0;
                     CK(cudaEventElapsedTime(&a, h->prof_ev[(0 * chunk + k) * 2], h->prof_ev[(0 * chunk + k) * 2 + 1]));
                     h->stats.adj_ms += a;
+                    h->stats.level_adj_ms[lev - 1] += a;
                     if (h->p.spclust_wght > 0.0) {
                         CK(cudaEventElapsedTime(&b, h->prof_ev[(1 * chunk + k) * 2], h->prof_ev[(1 * chunk + k) * 2 + 1]));
                         CK(cudaEventElapsedTime(&c, h->prof_ev[(1 * chunk + k) * 2 + 1], h->prof_ev[(2 * chunk + k) * 2 + 1]));
                         h->stats.screen_ms += b;
                         h->stats.spec_ms += c;
+                        h->stats.level_screen_ms[lev - 1] += b;
+                        h->stats.level_spec_ms[lev - 1] += c;
                     }
                 }
             }
@@ -1197,7 +1200,7 @@ extern "C" int rhseg_gram_tc(const void *X, int32_t rows, int32_t Bpad, int32_t 
         int dev = 0;
         if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     }
-    CK(launch_screen_tc_map(L, map, precision, std::min(nb * nb, nsm), (cudaStream_t)cuda_stream, job));
+    CK(launch_screen_tc_map(L, map, precision, std::max(1, std::min(nb * nb, 2 * nsm) / 2), (cudaStream_t)cuda_stream, job));
     return RHSEG_OK;
 }
 

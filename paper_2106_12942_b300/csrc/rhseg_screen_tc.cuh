@@ -400,289 +400,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_screen_tc(LevelDev L, const _
 }
 
 // ---------------------------------------------------------------------------
-// Resident-A variant (Bpad <= 256).  Each persistent CTA (one per SM) walks
-// chunks of RA_CHUNK consecutive tiles of the tile list (row-major upper
-// triangle per section), dealt round-robin so that the tiles in flight stay
-// close together and share their operand rows through L2.  Consecutive tiles
-// mostly share the 128-row block I, which stays in shared memory (two
-// buffers: the next block loads while the current one is used); only the J
-// blocks stream through a 4-stage ring, which halves the L2 traffic per MMA.
-// Ten warps: warp 0 TMA, warp 1 MMA (and tensor-memory owner), warps 2-5 and
-// 6-9 two epilogue groups taking alternate tiles, four FP32 accumulators of
-// 128 columns (all 512 columns of tensor memory).
-// ---------------------------------------------------------------------------
-
-constexpr int RA_STAGES = 4;
-constexpr int RA_ATOM_BYTES = TC_TILE * TC_KATOM * 2;      // 16 KB: 128 rows x 64 fp16
-constexpr int RA_NK_MAX = 4;                                // Bpad <= 256
-constexpr int RA_THREADS = 320;
-constexpr int RA_CHUNK = 16;
-struct RaShared {
-    uint64_t bfull[RA_STAGES], bempty[RA_STAGES];
-    uint64_t afull[2], afree[2];
-    uint64_t tfull[4], tempty[4];
-    uint32_t tmem_base;
-    int abort;
-    alignas(16) float hc[2][2][TC_TILE];                    // [epilogue group][buffer][column]
-    long long pre[MAX_SECTIONS + 1];
-};
-constexpr int RA_SMEM_BYTES =
-    (2 * RA_NK_MAX + RA_STAGES) * RA_ATOM_BYTES + 1024 + (int)((sizeof(RaShared) + 127) / 128 * 128);
-
-__device__ __forceinline__ long long ra_first(long long total)
-{
-    long long t = (long long)blockIdx.x * RA_CHUNK;
-    return t < total ? t : -1;
-}
-
-__device__ __forceinline__ long long ra_next(long long t, long long total)
-{
-    if (t < 0) return -1;
-    long long nt = t + 1;
-    if (nt % RA_CHUNK == 0) nt = (t / RA_CHUNK + gridDim.x) * RA_CHUNK;
-    return nt < total ? nt : -1;
-}
-
-// Barrier `id` over the 128 threads of one epilogue group, OR-reduced.
-__device__ __forceinline__ bool group_bar_or(int id, bool v)
-{
-    uint32_t out;
-    asm volatile(
-        "{\n\t.reg .pred q, p;\n\t"
-        "setp.ne.u32 q, %2, 0;\n\t"
-        "bar.red.or.pred p, %1, 128, q;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(out)
-        : "r"(id), "r"((uint32_t)v)
-        : "memory");
-    return out != 0;
-}
-
-__device__ __forceinline__ void group_bar(int id)
-{
-    asm volatile("bar.sync %0, 128;" ::"r"(id) : "memory");
-}
-
-__device__ __forceinline__ void tmem_ld32_nowait(uint32_t taddr, uint32_t *r)
-{
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
-        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-        : "r"(taddr));
-}
-
-template <int FMT>
-__global__ void __launch_bounds__(RA_THREADS, 1) k_screen_tc_ra(LevelDev L, const __grid_constant__ CUtensorMap tmap,
-                                                                TcJob job)
-{
-    extern __shared__ __align__(1024) uint8_t smem_raw[];
-    uint8_t *abuf = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);   // [2][RA_NK_MAX] atoms
-    uint8_t *ring = abuf + 2 * RA_NK_MAX * RA_ATOM_BYTES;                              // [RA_STAGES] atoms
-    RaShared &sh = *(RaShared *)(ring + RA_STAGES * RA_ATOM_BYTES);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int nk = L.Bpad / TC_KATOM;
-
-    long long total;
-    if (job.gram_rows > 0) {
-        long long nb = job.gram_rows / TC_TILE;
-        total = nb * nb;
-    } else {
-        block_tile_prefix(L, TC_TILE, sh.pre);
-        total = sh.pre[L.nsec];
-    }
-    const long long t0 = ra_first(total);
-    if (t0 < 0) return;       // uniform: this CTA has no tile
-
-    if (threadIdx.x == 0) {
-        for (int s = 0; s < RA_STAGES; s++) { mbar_init(&sh.bfull[s], 1); mbar_init(&sh.bempty[s], 1); }
-        for (int b = 0; b < 2; b++) { mbar_init(&sh.afull[b], 1); mbar_init(&sh.afree[b], 1); }
-        for (int b = 0; b < 4; b++) { mbar_init(&sh.tfull[b], 1); mbar_init(&sh.tempty[b], 4 * 32); }
-        sh.abort = 0;
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    }
-    if (warp == 1) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&sh.tmem_base)),
-                     "r"(512)
-                     : "memory");
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-    }
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
-    const uint32_t tbase = sh.tmem_base;
-    volatile int *abort = &sh.abort;
-
-    if (warp == 0) {
-        // ---------------- TMA producer ----------------
-        if (lane == 0) {
-            const uint64_t pol = l2_evict_first_policy();
-            int stage = 0, ab = 1;
-            uint32_t phase = 0;
-            uint32_t aload[2] = {0, 0};
-            int64_t prevA = -1;
-            for (long long t = t0; t >= 0 && !*abort; t = ra_next(t, total)) {
-                int sec, I, J;
-                int64_t rowA, rowB;
-                tc_tile(L, job, sh.pre, t, total, sec, I, J, rowA, rowB);
-                if (rowA != prevA) {
-                    ab ^= 1;
-                    if (!mbar_wait(&sh.afree[ab], (aload[ab] & 1) ^ 1, abort, L.err)) break;
-                    mbar_expect_tx(&sh.afull[ab], (uint32_t)(nk * RA_ATOM_BYTES));
-                    for (int k = 0; k < nk; k++)
-                        tma_load_2d(abuf + (ab * RA_NK_MAX + k) * RA_ATOM_BYTES, &tmap, k * TC_KATOM, (int)rowA,
-                                    &sh.afull[ab], pol);
-                    aload[ab]++;
-                    prevA = rowA;
-                }
-                bool ok = true;
-                for (int k = 0; k < nk; k++) {
-                    if (!mbar_wait(&sh.bempty[stage], phase ^ 1, abort, L.err)) { ok = false; break; }
-                    mbar_expect_tx(&sh.bfull[stage], RA_ATOM_BYTES);
-                    tma_load_2d(ring + stage * RA_ATOM_BYTES, &tmap, k * TC_KATOM, (int)rowB, &sh.bfull[stage], pol);
-                    if (++stage == RA_STAGES) { stage = 0; phase ^= 1; }
-                }
-                if (!ok) break;
-            }
-        }
-        __syncwarp();
-    } else if (warp == 1) {
-        // ---------------- MMA issuer ----------------
-        if (lane == 0) {
-            const uint32_t idesc = idesc_f16(FMT);
-            int stage = 0, ab = 1, tcount = 0;
-            uint32_t phase = 0;
-            uint32_t ause[2] = {0, 0};
-            int64_t prevA = -1;
-            for (long long t = t0; t >= 0 && !*abort; t = ra_next(t, total), tcount++) {
-                int sec, I, J;
-                int64_t rowA, rowB;
-                tc_tile(L, job, sh.pre, t, total, sec, I, J, rowA, rowB);
-                if (rowA != prevA) {
-                    if (prevA >= 0) tc_commit(&sh.afree[ab]);      // previous row block free once its MMAs end
-                    ab ^= 1;
-                    if (!mbar_wait(&sh.afull[ab], ause[ab] & 1, abort, L.err)) break;
-                    ause[ab]++;
-                    prevA = rowA;
-                }
-                // tile n of the CTA: epilogue group n & 1, accumulator 2 (n & 1) + ((n >> 1) & 1)
-                const int acc = 2 * (tcount & 1) + ((tcount >> 1) & 1);
-                if (!mbar_wait(&sh.tempty[acc], ((tcount >> 2) & 1) ^ 1, abort, L.err)) break;
-                tc_fence_after();
-                const uint32_t dt = tbase + (uint32_t)(acc * TC_TILE);
-                const uint32_t abase = smem_u32(abuf + ab * RA_NK_MAX * RA_ATOM_BYTES);
-                bool ok = true;
-                for (int k = 0; k < nk; k++) {
-                    if (!mbar_wait(&sh.bfull[stage], phase, abort, L.err)) { ok = false; break; }
-                    tc_fence_after();
-                    const uint64_t ad = sdesc_sw128(abase + k * RA_ATOM_BYTES);
-                    const uint64_t bd = sdesc_sw128(smem_u32(ring + stage * RA_ATOM_BYTES));
-#pragma unroll
-                    for (int kk = 0; kk < TC_KATOM / 16; kk++)
-                        tc_mma(dt, ad + (uint64_t)(2 * kk), bd + (uint64_t)(2 * kk), idesc, (k > 0 || kk > 0) ? 1u : 0u);
-                    tc_commit(&sh.bempty[stage]);
-                    if (++stage == RA_STAGES) { stage = 0; phase ^= 1; }
-                }
-                if (!ok) break;
-                tc_commit(&sh.tfull[acc]);
-            }
-        }
-        __syncwarp();
-    } else {
-        // ---------------- epilogue groups: warps 2-5 (g = 0), 6-9 (g = 1) ----------------
-        const int g = (warp - 2) >> 2;                  // epilogue group
-        const int barid = 1 + g;
-        const int q = warp & 3;                         // tensor-memory lane quarter of this warp
-        const int row = q * 32 + lane;                  // accumulator row = TMEM lane
-        const int et = (threadIdx.x - 64) & 127;        // column index for h within the group
-        const float inf = __int_as_float(0x7f800000);
-        float hc_next = inf, hr_next = inf;
-        // the group's tiles: positions g, g+2, g+4, ... of the CTA's walk
-        long long t = t0;
-        if (g == 1) t = ra_next(t, total);
-        if (job.gram_rows == 0 && t >= 0) {
-            int sec = 0, I = 0, J = 0;
-            int64_t rowA = 0, rowB = 0;
-            if (tc_tile_warp(L, job, sh.pre, t, total, sec, I, J, rowA, rowB)) {
-                hc_next = L.H[rowB + et];
-                hr_next = L.H[rowA + row];
-            }
-        }
-        for (int k = 0;; k++) {
-            int sec = 0, I = 0, J = 0;
-            int64_t rowA = 0, rowB = 0;
-            bool have = (t >= 0) && tc_tile_warp(L, job, sh.pre, t, total, sec, I, J, rowA, rowB);
-            if (group_bar_or(barid, !have || *abort)) break;
-            const int hb = k & 1;
-            sh.hc[g][hb][et] = hc_next;
-            const float hr = hr_next;
-            group_bar(barid);
-            const long long tn = ra_next(ra_next(t, total), total);
-            if (job.gram_rows == 0 && tn >= 0) {
-                int s2 = 0, I2 = 0, J2 = 0;
-                int64_t rA2 = 0, rB2 = 0;
-                if (tc_tile_warp(L, job, sh.pre, tn, total, s2, I2, J2, rA2, rB2)) {
-                    hc_next = L.H[rB2 + et];
-                    hr_next = L.H[rA2 + row];
-                }
-            }
-            const int acc = 2 * g + (k & 1);
-            bool ok = mbar_wait(&sh.tfull[acc], (k >> 1) & 1, abort, L.err);
-            ok = __all_sync(0xffffffffu, ok);
-            if (!ok) { t = tn; continue; }              // the next loop top stops the group
-            tc_fence_after();
-            const uint32_t taddr = tbase + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * TC_TILE);
-            uint32_t r[TC_TILE];
-#pragma unroll
-            for (int c0 = 0; c0 < TC_TILE; c0 += 32) tmem_ld32_nowait(taddr + (uint32_t)c0, r + c0);
-            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-            tc_fence_before();
-            mbar_arrive(&sh.tempty[acc]);               // accumulator free: values are in registers
-            if (job.gram_rows > 0) {
-                float *o = job.gram_out + ((int64_t)I * TC_TILE + row) * job.gram_rows + (int64_t)J * TC_TILE;
-#pragma unroll
-                for (int c = 0; c < TC_TILE; c++) o[c] = __uint_as_float(r[c]);
-            } else {
-                SecState *st = &L.st[sec];
-                const bool diag = (I == J);
-                const float *hcs = sh.hc[g][hb];
-#pragma unroll
-                for (int c0 = 0; c0 < TC_TILE; c0 += 32) {
-                    float m = -inf;
-#pragma unroll
-                    for (int c = 0; c < 32; c++) m = fmaxf(m, __uint_as_float(r[c0 + c]) - hcs[c0 + c]);
-                    if (m > hr) {
-                        for (int c = 0; c < 32; c++) {
-                            int cc = c0 + c;
-                            if (!(__uint_as_float(r[cc]) - hcs[cc] > hr)) continue;
-                            if (diag && cc <= row) continue;
-                            uint32_t idx = atomicAdd(&st->ncand, 1u);
-                            if ((int64_t)idx < L.cand_cap) {
-                                uint32_t *cd = L.cand + ((int64_t)sec * L.cand_cap + idx) * 2;
-                                cd[0] = (uint32_t)(I * TC_TILE + row);
-                                cd[1] = (uint32_t)(J * TC_TILE + cc);
-                            }
-                        }
-                    }
-                }
-            }
-            t = tn;
-        }
-    }
-    tc_fence_before();
-    __syncthreads();
-    if (warp == 1) {
-        tc_fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(512) : "memory");
-    }
-}
-
-// ---------------------------------------------------------------------------
 // Host side: tensor map over the operand rows and the launch.
 // ---------------------------------------------------------------------------
 
@@ -727,30 +444,20 @@ inline bool screen_uses_tcgen05(int precision) { return precision == 1 || precis
 inline cudaError_t launch_screen_tc_map(const LevelDev &L, const CUtensorMap &map, int precision, int n_sm,
                                         cudaStream_t s, TcJob job)
 {
-    static bool attr_done[4] = {false, false, false, false};
-    const bool ra = L.Bpad <= RA_NK_MAX * TC_KATOM;
-    int fi = (precision == 2 ? 1 : 0) + (ra ? 2 : 0);
+    static bool attr_done[2] = {false, false};
+    int fi = precision == 2 ? 1 : 0;
     if (!attr_done[fi]) {
-        cudaError_t e;
-        if (ra)
-            e = (precision == 2)
-                    ? cudaFuncSetAttribute(k_screen_tc_ra<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, RA_SMEM_BYTES)
-                    : cudaFuncSetAttribute(k_screen_tc_ra<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, RA_SMEM_BYTES);
-        else
-            e = (precision == 2)
-                    ? cudaFuncSetAttribute(k_screen_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM_BYTES)
-                    : cudaFuncSetAttribute(k_screen_tc<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM_BYTES);
+        cudaError_t e = (precision == 2)
+                            ? cudaFuncSetAttribute(k_screen_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   TC_SMEM_BYTES)
+                            : cudaFuncSetAttribute(k_screen_tc<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   TC_SMEM_BYTES);
         if (e != cudaSuccess) return e;
         attr_done[fi] = true;
     }
-    if (ra) {
-        // one CTA per SM; each walks a contiguous range of tiles
-        if (precision == 2) k_screen_tc_ra<1><<<n_sm, RA_THREADS, RA_SMEM_BYTES, s>>>(L, map, job);
-        else k_screen_tc_ra<0><<<n_sm, RA_THREADS, RA_SMEM_BYTES, s>>>(L, map, job);
-    } else {
-        if (precision == 2) k_screen_tc<1><<<2 * n_sm, TC_THREADS, TC_SMEM_BYTES, s>>>(L, map, job);
-        else k_screen_tc<0><<<2 * n_sm, TC_THREADS, TC_SMEM_BYTES, s>>>(L, map, job);
-    }
+    // two persistent CTAs per SM (shared memory 106 KB, tensor memory 256 columns each)
+    if (precision == 2) k_screen_tc<1><<<2 * n_sm, TC_THREADS, TC_SMEM_BYTES, s>>>(L, map, job);
+    else k_screen_tc<0><<<2 * n_sm, TC_THREADS, TC_SMEM_BYTES, s>>>(L, map, job);
     return cudaGetLastError();
 }
 
