@@ -744,6 +744,9 @@ static int run_impl(rhseg_handle *h)
         k_init_best<<<dim3(std::max(1, std::min(64, ceil_div(m0max, 8))), G.nsec), 256, 0, s>>>(D); h->nlaunch++;
         int32_t target = (lev == 1) ? h->p.conv_nregions : h->min_nr;
         k_init_section<<<G.nsec, STEP_THREADS, 0, s>>>(D, sc, target); h->nlaunch++;
+        if (h->p.spclust_wght > 0.0) {
+            k_write_rows<<<dim3(16, G.nsec), 256, 0, s>>>(D, sc); h->nlaunch++;
+        }
         CK(cudaGetLastError());
         if (lev == 1) {
             h->root_m0 = sth[0].m0;
@@ -766,6 +769,7 @@ static int run_impl(rhseg_handle *h)
                     launch_screen(h, D);
                     if (prof) CK(cudaEventRecord(h->prof_ev[(1 * chunk + k) * 2 + 1], s));
                     k_spec_step<<<G.nsec, STEP_THREADS, 0, s>>>(D, sc); h->nlaunch++;
+                    k_write_rows<<<dim3(16, G.nsec), 256, 0, s>>>(D, sc); h->nlaunch++;
                     if (prof) CK(cudaEventRecord(h->prof_ev[(2 * chunk + k) * 2 + 1], s));
                 }
             }

@@ -35,7 +35,7 @@ struct SecState {
     uint32_t ncand;        // candidates emitted in the current step
     int32_t madj, mspec;   // merges by kind
     int32_t nsplit;        // seam splits applied at the start of this level
-    int32_t pad0;
+    int32_t rows_from;     // > 0: the position list was rebuilt this iteration (old extent)
 };
 
 // Geometry and buffers of the level in flight (device pointers).  Arrays

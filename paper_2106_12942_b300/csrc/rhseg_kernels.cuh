@@ -345,14 +345,6 @@ __device__ __forceinline__ void mark_pos_dead(const LevelDev &L, int sec, int po
     else L.Af[L.poff[sec] + pos] = __int_as_float(0x7f800000);
 }
 
-template <typename T>
-__device__ void block_write_rows(const LevelDev &L, int sec, int mc_new, int pos_end, const ScreenConst &sc)
-{
-    int wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int pos = wid; pos < mc_new; pos += nw) warp_write_row<T>(L, sec, L.slot_of_pos[L.poff[sec] + pos], pos, sc);
-    for (int pos = mc_new + threadIdx.x; pos < pos_end; pos += blockDim.x) mark_pos_dead(L, sec, pos);
-}
-
 __device__ __forceinline__ void write_row_any(const LevelDev &L, int sec, int slot, int pos, const ScreenConst &sc)
 {
     switch (L.precision) {
@@ -363,15 +355,6 @@ __device__ __forceinline__ void write_row_any(const LevelDev &L, int sec, int sl
     }
 }
 
-__device__ __forceinline__ void block_write_rows_any(const LevelDev &L, int sec, int mc_new, int pos_end, const ScreenConst &sc)
-{
-    switch (L.precision) {
-    case 0: block_write_rows<double>(L, sec, mc_new, pos_end, sc); break;
-    case 1: block_write_rows<__half>(L, sec, mc_new, pos_end, sc); break;
-    case 2: block_write_rows<__nv_bfloat16>(L, sec, mc_new, pos_end, sc); break;
-    default: block_write_rows<float>(L, sec, mc_new, pos_end, sc); break;
-    }
-}
 
 // Per section: reference spectrum, positions, screen rows, counters.
 __global__ void __launch_bounds__(STEP_THREADS) k_init_section(LevelDev L, ScreenConst sc, int32_t target)
@@ -406,12 +389,12 @@ __global__ void __launch_bounds__(STEP_THREADS) k_init_section(LevelDev L, Scree
     for (int64_t w = threadIdx.x; w < (int64_t)m0 * W; w += blockDim.x) pc += __popc(A[w]);
     pc = block_sum_ll(pc, red);
     __syncthreads();
-    int pend = ((m0 + 127) / 128) * 128;
-    block_write_rows_any(L, sec, m0, pend, sc);
+    (void)sc;    // operand rows are written by k_write_rows (rows_from = m0)
     if (threadIdx.x == 0) {
         st->target = target;
         st->nadj = pc / 2;
         st->mc = m0;
+        st->rows_from = m0;
         st->done = (m0 <= target) ? 1 : 0;
         st->Kadj = __longlong_as_double(0x7FF0000000000000ll);
         st->tthr = st->Kadj;
@@ -425,15 +408,84 @@ __global__ void __launch_bounds__(STEP_THREADS) k_init_section(LevelDev L, Scree
 // HSEG step kernels
 // ---------------------------------------------------------------------------
 
+constexpr int PAIR_CAP = 1536;   // pair entries of one batched key phase
+constexpr int ROW_CAP = 256;     // rows whose best partner one merge recomputes (incl. the merged row)
+
 struct StepSmem {
     PairKey pk[32];
     long long ll[32];
+    SecState st;                               // section state for the kernel's lifetime
+    int32_t pi[PAIR_CAP], pj[PAIR_CAP];        // pair (row slot, partner slot)
+    int16_t prow[PAIR_CAP];                    // row index of the entry in rows[]
+    unsigned long long pkey[PAIR_CAP];         // K bits
+    int32_t npair;
+    int32_t rows[ROW_CAP];                     // rows[0] = the merged row
+    unsigned long long rowK[ROW_CAP], rowT[ROW_CAP];
+    int32_t nrows;
+    int32_t overflow;
     int32_t nb[NB_CHUNK_WORDS * 32];
     int32_t nnb;
-    int32_t rescan[RESCAN_CAP];
-    int32_t nrescan;
-    int32_t rescan_overflow;
 };
+
+// Exact keys of pairs [base, base + min(32, cnt - base)) of a smem list, by
+// one warp: the lanes run over the bands of one pair (two pairs interleaved)
+// and lane e keeps the sum of pair e; then every lane rounds its own pair's
+// quotient, so the divisions of 32 pairs run side by side.
+__device__ void warp_keys_batch(const LevelDev &L, int64_t ro, const int32_t *pi, const int32_t *pj,
+                                unsigned long long *pkey, int base, int cnt)
+{
+    const int lane = threadIdx.x & 31;
+    const int m = min(32, cnt - base);
+    u128 mine = {0, 0};
+    int64_t ni_m = 0, nj_m = 0;
+    int e = 0;
+    for (; e + 1 < m; e += 2) {
+        const int i0 = pi[base + e], j0 = pj[base + e], i1 = pi[base + e + 1], j1 = pj[base + e + 1];
+        const int64_t *S0 = L.S + (ro + i0) * L.Bs, *T0 = L.S + (ro + j0) * L.Bs;
+        const int64_t *S1 = L.S + (ro + i1) * L.Bs, *T1 = L.S + (ro + j1) * L.Bs;
+        const int64_t ni0 = L.n[ro + i0], nj0 = L.n[ro + j0], ni1 = L.n[ro + i1], nj1 = L.n[ro + j1];
+        u128 a0 = {0, 0}, a1 = {0, 0};
+        for (int b = lane; b < L.B; b += 32) {
+            int64_t d0 = nj0 * S0[b] - ni0 * T0[b];
+            int64_t d1 = nj1 * S1[b] - ni1 * T1[b];
+            a0 = u128_add(a0, u128_sq((uint64_t)(d0 < 0 ? -d0 : d0)));
+            a1 = u128_add(a1, u128_sq((uint64_t)(d1 < 0 ? -d1 : d1)));
+        }
+        a0 = warp_sum_u128(a0);
+        a1 = warp_sum_u128(a1);
+        if (lane == e) { mine = a0; ni_m = ni0; nj_m = nj0; }
+        if (lane == e + 1) { mine = a1; ni_m = ni1; nj_m = nj1; }
+    }
+    if (e < m) {
+        const int i0 = pi[base + e], j0 = pj[base + e];
+        const int64_t *S0 = L.S + (ro + i0) * L.Bs, *T0 = L.S + (ro + j0) * L.Bs;
+        const int64_t ni0 = L.n[ro + i0], nj0 = L.n[ro + j0];
+        u128 a0 = {0, 0};
+        for (int b = lane; b < L.B; b += 32) {
+            int64_t d0 = nj0 * S0[b] - ni0 * T0[b];
+            a0 = u128_add(a0, u128_sq((uint64_t)(d0 < 0 ? -d0 : d0)));
+        }
+        a0 = warp_sum_u128(a0);
+        if (lane == e) { mine = a0; ni_m = ni0; nj_m = nj0; }
+    }
+    if (lane < m) {
+        u128 D = u128_mul64((uint64_t)ni_m * (uint64_t)nj_m, (uint64_t)(ni_m + nj_m));
+        pkey[base + lane] = dbits(div_rn_u128(mine, D, L.err));
+    }
+}
+
+__device__ __forceinline__ void set_best(const LevelDev &L, int64_t ro, int r, unsigned long long K,
+                                         unsigned long long T)
+{
+    if (K == RHSEG_KEY_NONE) {
+        L.bestK[ro + r] = RHSEG_KEY_NONE;
+        L.bestP[ro + r] = -1;
+    } else {
+        uint32_t lo = (uint32_t)(T >> 32), hi = (uint32_t)T;
+        L.bestK[ro + r] = K;
+        L.bestP[ro + r] = (int32_t)(lo == (uint32_t)r ? hi : lo);
+    }
+}
 
 // Exact best adjacent partner of slot r recomputed by one warp (the row's
 // words are read by the lanes, set bits visited in order, one key per bit).
@@ -468,42 +520,96 @@ __device__ void warp_rescan_row(const LevelDev &L, int sec, int r)
     }
 }
 
-// Merge slot b into slot a (a < b, so a keeps the smaller ID).  Whole block.
-__device__ void block_merge(const LevelDev &L, int sec, int a, int b, double K, int kind,
+// Best adjacent partners after merging b into a, when the batched lists do
+// not fit: the merged row by warps over its neighbours, re-scans one warp
+// per row.
+__device__ void block_best_update_slow(const LevelDev &L, int sec, int a, int b, StepSmem &sm)
+{
+    const int64_t ro = L.roff[sec];
+    const int W = L.W[sec];
+    const uint32_t *rowA = L.adj + L.aoff[sec] + (int64_t)a * W;
+    const int tid = threadIdx.x, nt = blockDim.x, wid = tid >> 5, nw = nt >> 5, lane = tid & 31;
+    const int64_t *Sa = L.S + (ro + a) * L.Bs;
+    const int64_t na = L.n[ro + a];
+    PairKey best = pk_none();
+    // neighbours of a: their key with a; rows whose best partner was a or b
+    // are re-scanned afterwards (listed in sm.nb, processed per chunk)
+    for (int w0 = 0; w0 < W; w0 += NB_CHUNK_WORDS) {
+        __syncthreads();
+        if (tid == 0) sm.nnb = 0;
+        __syncthreads();
+        for (int w = w0 + tid; w < min(W, w0 + NB_CHUNK_WORDS); w += nt) {
+            uint32_t bits = rowA[w];
+            while (bits) {
+                int q = w * 32 + __ffs(bits) - 1;
+                bits &= bits - 1;
+                sm.nb[atomicAdd(&sm.nnb, 1)] = q;
+            }
+        }
+        __syncthreads();
+        const int cnt = sm.nnb;
+        for (int t = wid; t < cnt; t += nw) {
+            const int r = sm.nb[t];
+            const double Kr = warp_key(Sa, na, L.S + (ro + r) * L.Bs, L.n[ro + r], L.B, L.err);
+            const PairKey c = pk_make(dbits(Kr), a, r);
+            if (pk_less(c, best)) best = c;
+            int bp = L.bestP[ro + r];
+            bool rescan = (bp == a || bp == b || bp < 0);
+            if (!rescan && lane == 0) {
+                PairKey old = pk_make(L.bestK[ro + r], r, bp);
+                PairKey nc = pk_make(dbits(Kr), r, a);
+                if (pk_less(nc, old)) { L.bestK[ro + r] = nc.k; L.bestP[ro + r] = a; }
+            }
+            __syncwarp();
+            if (rescan) warp_rescan_row(L, sec, r);
+        }
+    }
+    best = block_min_pk(best, sm.pk);
+    if (tid == 0) {
+        L.bestK[ro + a] = best.k;
+        L.bestP[ro + a] = (best.k == RHSEG_KEY_NONE) ? -1 : (int32_t)(best.lo == (uint32_t)a ? best.hi : best.lo);
+    }
+    __syncthreads();
+}
+
+// Merge slot b into slot a (a < b, so a keeps the smaller ID).  Whole block;
+// st is the block's shared copy of the section state.
+__device__ void block_merge(const LevelDev &L, int sec, SecState &st, int a, int b, double K, int kind,
                             const ScreenConst &sc, StepSmem &sm)
 {
-    SecState *st = &L.st[sec];
-    int64_t ro = L.roff[sec];
-    int W = L.W[sec];
+    const int64_t ro = L.roff[sec];
+    const int W = L.W[sec];
     uint32_t *A = L.adj + L.aoff[sec];
     uint32_t *rowA = A + (int64_t)a * W;
     uint32_t *rowB = A + (int64_t)b * W;
-    int tid = threadIdx.x, nt = blockDim.x;
-    int ab = (rowA[b >> 5] >> (b & 31)) & 1;
+    const int tid = threadIdx.x, nt = blockDim.x, wid = tid >> 5, nw = nt >> 5;
+    const int ab = (rowA[b >> 5] >> (b & 31)) & 1;
     long long pa = 0, pb = 0;
     for (int w = tid; w < W; w += nt) { pa += __popc(rowA[w]); pb += __popc(rowB[w]); }
     pa = block_sum_ll(pa, sm.ll);
     pb = block_sum_ll(pb, sm.ll);
     __syncthreads();
-    // features (exact integers)
+    // features (exact integers) and bookkeeping
     for (int k = tid; k < L.Bs; k += nt) L.S[(ro + a) * L.Bs + k] += L.S[(ro + b) * L.Bs + k];
     if (tid == 0) {
-        L.n[ro + a] += L.n[ro + b];
+        const int64_t na = L.n[ro + a], nb = L.n[ro + b];
+        const uint32_t ida = L.rid[ro + a], idb = L.rid[ro + b];
+        L.n[ro + a] = na + nb;
         L.alive[ro + b] = 0;
         L.parent[ro + b] = (int32_t)(ro + a);
-        int ord = ++st->nmerge;
-        if (kind == 0) st->madj += 1; else st->mspec += 1;
+        const int ord = ++st.nmerge;
+        if (kind == 0) st.madj += 1; else st.mspec += 1;
         L.absorbed_at[ro + b] = ord;
         L.bestK[ro + b] = RHSEG_KEY_NONE;
         L.bestP[ro + b] = -1;
-        st->count -= 1;
+        st.count -= 1;
         rhseg_merge m;
-        m.level = L.level; m.section = sec; m.step = st->iter; m.kind = kind;
-        m.survivor_id = L.rid[ro + a]; m.absorbed_id = L.rid[ro + b];
+        m.level = L.level; m.section = sec; m.step = st.iter; m.kind = kind;
+        m.survivor_id = ida; m.absorbed_id = idb;
         m.key = K; m.dissim = sqrt(K);
-        m.nregions_after = st->count; m.pad = 0;
-        ((rhseg_merge *)L.log)[L.loff[sec] + st->log_n] = m;
-        st->log_n += 1;
+        m.nregions_after = st.count; m.pad = 0;
+        ((rhseg_merge *)L.log)[L.loff[sec] + st.log_n] = m;
+        st.log_n += 1;
     }
     // adjacency: row a |= row b, neighbours of b now point to a
     for (int w = tid; w < W; w += nt) rowA[w] |= rowB[w];
@@ -530,108 +636,114 @@ __device__ void block_merge(const LevelDev &L, int sec, int a, int b, double K, 
     for (int w = tid; w < W; w += nt) pn += __popc(rowA[w]);
     pn = block_sum_ll(pn, sm.ll);
     if (tid == 0) {
-        st->nadj = st->nadj - pa - pb + ab + pn;
-        sm.nrescan = 0;
-        sm.rescan_overflow = 0;
+        st.nadj = st.nadj - pa - pb + ab + pn;
+        sm.npair = 0;
+        sm.nrows = 1;
+        sm.rows[0] = a;
+        sm.overflow = 0;
     }
     __syncthreads();
-    // exact best partners: row a in full, neighbours of a incrementally
-    const int64_t *Sa = L.S + (ro + a) * L.Bs;
-    int64_t na = L.n[ro + a];
-    int wid = tid >> 5, nw = nt >> 5, lane = tid & 31;
-    PairKey best = pk_none();
-    for (int w0 = 0; w0 < W; w0 += NB_CHUNK_WORDS) {
-        __syncthreads();
-        if (tid == 0) sm.nnb = 0;
-        __syncthreads();
-        for (int w = w0 + tid; w < min(W, w0 + NB_CHUNK_WORDS); w += nt) {
-            uint32_t bits = rowA[w];
-            while (bits) {
-                int q = w * 32 + __ffs(bits) - 1;
-                bits &= bits - 1;
-                sm.nb[atomicAdd(&sm.nnb, 1)] = q;
+    // ---- exact best partners: one batched key phase ----
+    // entries of row 0: (a, r) for every neighbour r of a
+    for (int w = tid; w < W; w += nt) {
+        uint32_t bits = rowA[w];
+        while (bits) {
+            int r = w * 32 + __ffs(bits) - 1;
+            bits &= bits - 1;
+            int idx = atomicAdd(&sm.npair, 1);
+            if (idx < PAIR_CAP) { sm.pi[idx] = a; sm.pj[idx] = r; sm.prow[idx] = 0; }
+            else sm.overflow = 1;
+        }
+    }
+    __syncthreads();
+    if (!sm.overflow) {
+        // rows whose best partner was a or b are recomputed in full
+        const int n0 = sm.npair;
+        for (int e = tid; e < n0; e += nt) {
+            const int r = sm.pj[e];
+            const int bp = L.bestP[ro + r];
+            if (bp == a || bp == b || bp < 0) {
+                int k = atomicAdd(&sm.nrows, 1);
+                if (k < ROW_CAP) sm.rows[k] = r; else sm.overflow = 1;
             }
         }
         __syncthreads();
-        int cnt = sm.nnb;
-        for (int t = wid; t < cnt; t += nw) {
-            int r = sm.nb[t];
-            double Kr = warp_key(Sa, na, L.S + (ro + r) * L.Bs, L.n[ro + r], L.B, L.err);
-            PairKey c = pk_make(dbits(Kr), a, r);
-            if (pk_less(c, best)) best = c;
-            if (lane == 0) {
-                int bp = L.bestP[ro + r];
-                if (bp == a || bp == b || bp < 0) {
-                    int k = atomicAdd(&sm.nrescan, 1);
-                    if (k < RESCAN_CAP) sm.rescan[k] = r; else sm.rescan_overflow = 1;
-                } else {
+        const int nr = min(sm.nrows, ROW_CAP);
+        if (!sm.overflow) {
+            for (int64_t f = tid; f < (int64_t)(nr - 1) * W; f += nt) {
+                const int k = 1 + (int)(f / W), w = (int)(f % W);
+                const int r = sm.rows[k];
+                uint32_t bits = A[(int64_t)r * W + w];
+                while (bits) {
+                    int q = w * 32 + __ffs(bits) - 1;
+                    bits &= bits - 1;
+                    int idx = atomicAdd(&sm.npair, 1);
+                    if (idx < PAIR_CAP) { sm.pi[idx] = r; sm.pj[idx] = q; sm.prow[idx] = (int16_t)k; }
+                    else sm.overflow = 1;
+                }
+            }
+        }
+        __syncthreads();
+    }
+    if (sm.overflow) {
+        block_best_update_slow(L, sec, a, b, sm);
+    } else {
+        const int np = sm.npair, nr = sm.nrows;
+        for (int k = tid; k < nr; k += nt) { sm.rowK[k] = RHSEG_KEY_NONE; sm.rowT[k] = ~0ull; }
+        for (int base = wid * 32; base < np; base += nw * 32) warp_keys_batch(L, ro, sm.pi, sm.pj, sm.pkey, base, np);
+        __syncthreads();
+        for (int e = tid; e < np; e += nt) atomicMin(&sm.rowK[sm.prow[e]], sm.pkey[e]);
+        __syncthreads();
+        for (int e = tid; e < np; e += nt) {
+            const int k = sm.prow[e];
+            if (sm.pkey[e] == sm.rowK[k]) {
+                const uint32_t i = (uint32_t)sm.pi[e], j = (uint32_t)sm.pj[e];
+                const unsigned long long t = ((unsigned long long)min(i, j) << 32) | max(i, j);
+                atomicMin(&sm.rowT[k], t);
+            }
+            if (k == 0) {
+                // neighbour r of a whose best partner is neither a nor b: compare with K(r, a)
+                const int r = sm.pj[e];
+                const int bp = L.bestP[ro + r];
+                if (!(bp == a || bp == b || bp < 0)) {
                     PairKey old = pk_make(L.bestK[ro + r], r, bp);
-                    PairKey nc = pk_make(dbits(Kr), r, a);
+                    PairKey nc = pk_make(sm.pkey[e], r, a);
                     if (pk_less(nc, old)) { L.bestK[ro + r] = nc.k; L.bestP[ro + r] = a; }
                 }
             }
         }
+        __syncthreads();
+        for (int k = tid; k < nr; k += nt) set_best(L, ro, sm.rows[k], sm.rowK[k], sm.rowT[k]);
+        __syncthreads();
     }
-    best = block_min_pk(best, sm.pk);
-    if (tid == 0) {
-        L.bestK[ro + a] = best.k;
-        L.bestP[ro + a] = (best.k == RHSEG_KEY_NONE) ? -1 : (int32_t)(best.lo == (uint32_t)a ? best.hi : best.lo);
-    }
-    __syncthreads();
-    int nres = min(sm.nrescan, RESCAN_CAP);
-    int ovf = sm.rescan_overflow;
-    if (!ovf) {
-        // rows whose best partner was a or b: one warp per row
-        for (int k = wid; k < nres; k += nw) warp_rescan_row(L, sec, sm.rescan[k]);
-    } else {
-        // too many such rows to list: re-scan every neighbour of a
-        for (int w0 = 0; w0 < W; w0 += NB_CHUNK_WORDS) {
-            __syncthreads();
-            if (tid == 0) sm.nnb = 0;
-            __syncthreads();
-            for (int w = w0 + tid; w < min(W, w0 + NB_CHUNK_WORDS); w += nt) {
-                uint32_t bits = rowA[w];
-                while (bits) {
-                    int q = w * 32 + __ffs(bits) - 1;
-                    bits &= bits - 1;
-                    sm.nb[atomicAdd(&sm.nnb, 1)] = q;
-                }
-            }
-            __syncthreads();
-            int cnt = sm.nnb;
-            for (int k = wid; k < cnt; k += nw) warp_rescan_row(L, sec, sm.nb[k]);
-        }
-    }
-    __syncthreads();
     // screen rows of a (new features) and b (dead)
-    int pa_pos = L.pos_of_slot[ro + a], pb_pos = L.pos_of_slot[ro + b];
+    const int pa_pos = L.pos_of_slot[ro + a], pb_pos = L.pos_of_slot[ro + b];
     if (wid == 0) write_row_any(L, sec, a, pa_pos, sc);
     if (tid == 32) mark_pos_dead(L, sec, pb_pos);
     __syncthreads();
 }
 
-// Stable compaction of the screen positions to the live slots.
-__device__ void block_compact(const LevelDev &L, int sec, const ScreenConst &sc, StepSmem &sm)
+// New stable position list of the live slots (the screen's operand rows are
+// then rewritten by k_write_rows).
+__device__ void block_compact_positions(const LevelDev &L, int sec, SecState &st)
 {
-    SecState *st = &L.st[sec];
-    int m0 = st->m0;
-    int64_t ro = L.roff[sec];
-    int old_mc = st->mc;
+    const int m0 = st.m0;
+    const int64_t ro = L.roff[sec];
     __shared__ int32_t wcnt[32];
     __shared__ int32_t base;
     if (threadIdx.x == 0) base = 0;
     __syncthreads();
-    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (int c = 0; c < m0; c += blockDim.x) {
-        int i = c + threadIdx.x;
-        int f = (i < m0) ? L.alive[ro + i] : 0;
-        unsigned bal = __ballot_sync(0xffffffffu, f);
+        const int i = c + threadIdx.x;
+        const int f = (i < m0) ? L.alive[ro + i] : 0;
+        const unsigned bal = __ballot_sync(0xffffffffu, f);
         if (lane == 0) wcnt[wid] = __popc(bal);
         __syncthreads();
         int off = 0, tot = 0;
         for (int k = 0; k < nw; k++) { if (k < wid) off += wcnt[k]; tot += wcnt[k]; }
         if (f) {
-            int pos = base + off + __popc(bal & ((1u << lane) - 1));
+            const int pos = base + off + __popc(bal & ((1u << lane) - 1));
             L.pos_of_slot[ro + i] = pos;
             L.slot_of_pos[L.poff[sec] + pos] = i;
         }
@@ -639,37 +751,56 @@ __device__ void block_compact(const LevelDev &L, int sec, const ScreenConst &sc,
         if (threadIdx.x == 0) base += tot;
         __syncthreads();
     }
-    int mc = base;
-    int pend = ((old_mc + 127) / 128) * 128;
-    block_write_rows_any(L, sec, mc, pend, sc);
+    if (threadIdx.x == 0) {
+        st.rows_from = st.mc;       // old extent: positions past the new end are marked dead
+        st.mc = base;
+    }
     __syncthreads();
-    if (threadIdx.x == 0) st->mc = mc;
-    __syncthreads();
+}
+
+// Operand rows of every position of the sections whose position list was
+// (re)built this iteration; many blocks per section, one warp per row.
+__global__ void __launch_bounds__(256) k_write_rows(LevelDev L, ScreenConst sc)
+{
+    const int sec = blockIdx.y;
+    if (sec >= L.nsec) return;
+    const SecState &st = L.st[sec];
+    const int old = st.rows_from;
+    if (old <= 0 || st.done) return;
+    const int mc = st.mc;
+    const int pend = ((max(old, mc) + 127) / 128) * 128;
+    const int wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int gw = blockIdx.x * nw + wid, ngw = gridDim.x * nw;
+    for (int pos = gw; pos < mc; pos += ngw) write_row_any(L, sec, L.slot_of_pos[L.poff[sec] + pos], pos, sc);
+    for (int pos = mc + blockIdx.x * blockDim.x + threadIdx.x; pos < pend; pos += gridDim.x * blockDim.x)
+        mark_pos_dead(L, sec, pos);
 }
 
 // Step 2 of HSEG: merge the adjacent pair of minimum key.
 __global__ void __launch_bounds__(STEP_THREADS, 2) k_adj_step(LevelDev L, ScreenConst sc)
 {
-    int sec = blockIdx.x;
+    const int sec = blockIdx.x;
     if (sec >= L.nsec) return;
     __shared__ StepSmem sm;
-    SecState *st = &L.st[sec];
-    if (st->done) return;
+    if (threadIdx.x == 0) sm.st = L.st[sec];
     __syncthreads();
-    if (st->count <= st->target) {
-        if (threadIdx.x == 0) { st->done = 1; st->spec_pending = 0; }
+    SecState &st = sm.st;
+    if (st.done) return;
+    if (st.count <= st.target) {
+        if (threadIdx.x == 0) { st.done = 1; st.spec_pending = 0; st.rows_from = 0; L.st[sec] = st; }
         return;
     }
-    int64_t ro = L.roff[sec];
-    int m0 = st->m0;
-    if (threadIdx.x == 0) { st->iter += 1; st->pairs += st->nadj; }
+    const int64_t ro = L.roff[sec];
+    const int m0 = st.m0;
+    __syncthreads();
+    if (threadIdx.x == 0) { st.iter += 1; st.pairs += st.nadj; st.rows_from = 0; }
     PairKey best = pk_none();
     for (int i = threadIdx.x; i < m0; i += blockDim.x) {
         // absorbed slots carry RHSEG_KEY_NONE
-        uint64_t k = L.bestK[ro + i];
-        int32_t bp = L.bestP[ro + i];
+        const uint64_t k = L.bestK[ro + i];
+        const int32_t bp = L.bestP[ro + i];
         if (k == RHSEG_KEY_NONE) continue;
-        PairKey c = pk_make(k, i, bp);
+        const PairKey c = pk_make(k, i, bp);
         if (pk_less(c, best)) best = c;
     }
     best = block_min_pk(best, sm.pk);
@@ -678,115 +809,136 @@ __global__ void __launch_bounds__(STEP_THREADS, 2) k_adj_step(LevelDev L, Screen
     double Kadj = __longlong_as_double(0x7FF0000000000000ll);
     if (best.k != RHSEG_KEY_NONE) {
         Kadj = __longlong_as_double((long long)best.k);
-        block_merge(L, sec, (int)best.lo, (int)best.hi, Kadj, 0, sc, sm);
+        block_merge(L, sec, st, (int)best.lo, (int)best.hi, Kadj, 0, sc, sm);
         merged = 1;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        st->merged_adj = merged;
-        st->Kadj = Kadj;
-        if (merged && st->count <= st->target) {
-            st->done = 1;
-            st->spec_pending = 0;
+        st.merged_adj = merged;
+        st.Kadj = Kadj;
+        if (merged && st.count <= st.target) {
+            st.done = 1;
+            st.spec_pending = 0;
         } else if (L.w > 0.0) {
-            st->spec_pending = 1;
-            st->tthr = merged ? L.ww * Kadj : Kadj;
-            st->ncand = 0;
+            st.spec_pending = 1;
+            st.tthr = merged ? L.ww * Kadj : Kadj;
+            st.ncand = 0;
         } else {
-            st->spec_pending = 0;
-            if (!merged) { st->stalled = 1; st->done = 1; }
+            st.spec_pending = 0;
+            if (!merged) { st.stalled = 1; st.done = 1; }
         }
     }
+    __syncthreads();
     // per-row threshold terms of this step's tensor-core screen
-    if (L.H != nullptr) {
-        __syncthreads();
-        if (st->spec_pending) {
-            const float Tf = __double2float_ru(st->tthr);
-            const int mc = st->mc;
-            const int pend = ((mc + 127) / 128) * 128;
-            const int64_t pb = L.poff[sec];
-            const float inf = __int_as_float(0x7f800000);
-            for (int pos = threadIdx.x; pos < pend; pos += blockDim.x)
-                L.H[pb + pos] = (pos < mc) ? 0.5f * (L.Af[pb + pos] - Tf * L.kf[pb + pos]) : inf;
-        }
+    if (L.H != nullptr && st.spec_pending) {
+        const float Tf = __double2float_ru(st.tthr);
+        const int mc = st.mc;
+        const int pend = ((mc + 127) / 128) * 128;
+        const int64_t pb = L.poff[sec];
+        const float inf = __int_as_float(0x7f800000);
+        for (int pos = threadIdx.x; pos < pend; pos += blockDim.x)
+            L.H[pb + pos] = (pos < mc) ? 0.5f * (L.Af[pb + pos] - Tf * L.kf[pb + pos]) : inf;
     }
+    __syncthreads();
+    if (threadIdx.x == 0) L.st[sec] = st;
 }
 
 // Step 3 of HSEG: exact re-check of the screen's candidates (or of every
 // non-adjacent pair when no finite threshold exists or the candidate buffer
-// overflowed), merge of the minimum if below the threshold.
+// overflowed), merge of the minimum if below the threshold; then, when
+// enough regions died, a new compact position list for the screen.
 __global__ void __launch_bounds__(STEP_THREADS, 2) k_spec_step(LevelDev L, ScreenConst sc)
 {
-    int sec = blockIdx.x;
+    const int sec = blockIdx.x;
     if (sec >= L.nsec) return;
     __shared__ StepSmem sm;
-    SecState *st = &L.st[sec];
-    if (!st->spec_pending) return;
+    if (threadIdx.x == 0) sm.st = L.st[sec];
     __syncthreads();
-    int64_t ro = L.roff[sec];
-    int m0 = st->m0;
-    int W = L.W[sec];
+    SecState &st = sm.st;
+    if (!st.spec_pending) return;
+    const int64_t ro = L.roff[sec];
+    const int m0 = st.m0;
+    const int W = L.W[sec];
     const uint32_t *A = L.adj + L.aoff[sec];
-    double t = st->tthr;
-    int count = st->count;
-    int mc = st->mc;
-    uint32_t ncand = st->ncand;
-    bool finite = t < __longlong_as_double(0x7FF0000000000000ll);
-    bool exhaustive = !finite || (int64_t)ncand > L.cand_cap;
-    int wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const double t = st.tthr;
+    const int count = st.count;
+    const int mc = st.mc;
+    const uint32_t ncand = st.ncand;
+    const bool finite = t < __longlong_as_double(0x7FF0000000000000ll);
+    const bool exhaustive = !finite || (int64_t)ncand > L.cand_cap;
+    const int tid = threadIdx.x, nt = blockDim.x, wid = tid >> 5, nw = nt >> 5;
+    const uint64_t tbits = dbits(t);
     PairKey best = pk_none();
+    long long ntrue = 0;
     if (!exhaustive) {
         const uint32_t *cand = L.cand + (int64_t)sec * L.cand_cap * 2;
         const int32_t *sop = L.slot_of_pos + L.poff[sec];
-        for (uint32_t c = wid; c < ncand; c += nw) {
-            int i = sop[cand[2 * c]], j = sop[cand[2 * c + 1]];
-            if (i == j || !L.alive[ro + i] || !L.alive[ro + j]) continue;
-            if ((A[(int64_t)i * W + (j >> 5)] >> (j & 31)) & 1) continue;
-            double K = warp_key(L.S + (ro + i) * L.Bs, L.n[ro + i], L.S + (ro + j) * L.Bs, L.n[ro + j], L.B, L.err);
-            if (!(K < t)) continue;
-            if ((threadIdx.x & 31) == 0) atomicAdd((unsigned long long *)&st->cands_true, 1ull);
-            PairKey pc = pk_make(dbits(K), i, j);
-            if (pk_less(pc, best)) best = pc;
+        for (uint32_t c0 = 0; c0 < ncand; c0 += PAIR_CAP) {
+            __syncthreads();
+            if (tid == 0) sm.npair = 0;
+            __syncthreads();
+            for (uint32_t c = c0 + tid; c < min(ncand, c0 + PAIR_CAP); c += nt) {
+                const int i = sop[cand[2 * c]], j = sop[cand[2 * c + 1]];
+                if (i == j || !L.alive[ro + i] || !L.alive[ro + j]) continue;
+                if ((A[(int64_t)i * W + (j >> 5)] >> (j & 31)) & 1) continue;
+                const int idx = atomicAdd(&sm.npair, 1);
+                sm.pi[idx] = min(i, j);
+                sm.pj[idx] = max(i, j);
+            }
+            __syncthreads();
+            const int np = sm.npair;
+            for (int base = wid * 32; base < np; base += nw * 32) warp_keys_batch(L, ro, sm.pi, sm.pj, sm.pkey, base, np);
+            __syncthreads();
+            for (int e = tid; e < np; e += nt) {
+                const uint64_t kb = sm.pkey[e];
+                if (!(kb < tbits)) continue;          // K < t (both non-negative binary64)
+                ntrue++;
+                const PairKey pc = pk_make(kb, sm.pi[e], sm.pj[e]);
+                if (pk_less(pc, best)) best = pc;
+            }
         }
     } else {
         // every unordered pair of live, non-adjacent slots
-        int64_t npair = (int64_t)m0 * (m0 - 1) / 2;
+        const int64_t npair = (int64_t)m0 * (m0 - 1) / 2;
         for (int64_t e = wid; e < npair; e += nw) {
-            // decode e -> (i, j), i < j, row-major upper triangle
             int64_t i = (int64_t)((2.0 * m0 - 1 - sqrt((2.0 * m0 - 1) * (2.0 * m0 - 1) - 8.0 * e)) / 2);
             while (i > 0 && i * (2 * m0 - i - 1) / 2 > e) i--;
             while ((i + 1) * (2 * m0 - i - 2) / 2 <= e) i++;
-            int64_t j = e - i * (2 * m0 - i - 1) / 2 + i + 1;
+            const int64_t j = e - i * (2 * m0 - i - 1) / 2 + i + 1;
             if (!L.alive[ro + i] || !L.alive[ro + j]) continue;
             if ((A[i * W + (j >> 5)] >> (j & 31)) & 1) continue;
-            double K = warp_key(L.S + (ro + i) * L.Bs, L.n[ro + i], L.S + (ro + j) * L.Bs, L.n[ro + j], L.B, L.err);
+            const double K = warp_key(L.S + (ro + i) * L.Bs, L.n[ro + i], L.S + (ro + j) * L.Bs, L.n[ro + j], L.B, L.err);
             if (!(K < t)) continue;
-            PairKey pc = pk_make(dbits(K), (int)i, (int)j);
+            const PairKey pc = pk_make(dbits(K), (int)i, (int)j);
             if (pk_less(pc, best)) best = pc;
         }
     }
+    ntrue = block_sum_ll(ntrue, sm.ll);
     best = block_min_pk(best, sm.pk);
     __syncthreads();
-    if (threadIdx.x == 0) {
-        st->pairs += (int64_t)count * (count - 1) / 2 - st->nadj;
-        st->cands += exhaustive ? 0 : (int64_t)ncand;
-        st->fallbacks += exhaustive ? 1 : 0;
-        if (!exhaustive) st->screened += (int64_t)mc * (mc - 1) / 2;
+    if (tid == 0) {
+        st.pairs += (int64_t)count * (count - 1) / 2 - st.nadj;
+        st.cands += exhaustive ? 0 : (int64_t)ncand;
+        st.cands_true += ntrue;
+        st.fallbacks += exhaustive ? 1 : 0;
+        if (!exhaustive) st.screened += (int64_t)mc * (mc - 1) / 2;
     }
     int merged = 0;
     if (best.k != RHSEG_KEY_NONE) {
-        block_merge(L, sec, (int)best.lo, (int)best.hi, __longlong_as_double((long long)best.k), 1, sc, sm);
+        block_merge(L, sec, st, (int)best.lo, (int)best.hi, __longlong_as_double((long long)best.k), 1, sc, sm);
         merged = 1;
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        st->spec_pending = 0;
-        st->ncand = 0;
-        if (!merged && !st->merged_adj) { st->stalled = 1; st->done = 1; }
-        if (st->count <= st->target) st->done = 1;
+    if (tid == 0) {
+        st.spec_pending = 0;
+        st.ncand = 0;
+        if (!merged && !st.merged_adj) { st.stalled = 1; st.done = 1; }
+        if (st.count <= st.target) st.done = 1;
     }
     __syncthreads();
-    if (!st->done && st->count <= (st->mc * 7) / 8 && st->mc > 128) block_compact(L, sec, sc, sm);
+    if (!st.done && st.count <= (st.mc * 7) / 8 && st.mc > 128) block_compact_positions(L, sec, st);
+    __syncthreads();
+    if (tid == 0) L.st[sec] = st;
 }
 
 // ---------------------------------------------------------------------------
