@@ -427,51 +427,59 @@ struct StepSmem {
     int32_t nnb;
 };
 
-// Exact keys of pairs [base, base + min(32, cnt - base)) of a smem list, by
-// one warp: the lanes run over the bands of one pair (two pairs interleaved)
-// and lane e keeps the sum of pair e; then every lane rounds its own pair's
-// quotient, so the divisions of 32 pairs run side by side.
+// Exact keys of the pairs wid, wid + nw, wid + 2 nw, ... (at most 32 of them)
+// of a shared-memory list, computed by warp `wid` of `nw`: the lanes run
+// over the bands of four pairs at a time (independent loads in flight) and
+// lane e keeps the sum of the warp's pair e; then every lane rounds its own
+// pair's quotient, so the divisions run side by side.
 __device__ void warp_keys_batch(const LevelDev &L, int64_t ro, const int32_t *pi, const int32_t *pj,
-                                unsigned long long *pkey, int base, int cnt)
+                                unsigned long long *pkey, int first, int stride, int cnt)
 {
     const int lane = threadIdx.x & 31;
-    const int m = min(32, cnt - base);
+    const int m = (cnt > first) ? min(32, (cnt - first + stride - 1) / stride) : 0;
     u128 mine = {0, 0};
     int64_t ni_m = 0, nj_m = 0;
-    int e = 0;
-    for (; e + 1 < m; e += 2) {
-        const int i0 = pi[base + e], j0 = pj[base + e], i1 = pi[base + e + 1], j1 = pj[base + e + 1];
-        const int64_t *S0 = L.S + (ro + i0) * L.Bs, *T0 = L.S + (ro + j0) * L.Bs;
-        const int64_t *S1 = L.S + (ro + i1) * L.Bs, *T1 = L.S + (ro + j1) * L.Bs;
-        const int64_t ni0 = L.n[ro + i0], nj0 = L.n[ro + j0], ni1 = L.n[ro + i1], nj1 = L.n[ro + j1];
-        u128 a0 = {0, 0}, a1 = {0, 0};
-        for (int b = lane; b < L.B; b += 32) {
-            int64_t d0 = nj0 * S0[b] - ni0 * T0[b];
-            int64_t d1 = nj1 * S1[b] - ni1 * T1[b];
-            a0 = u128_add(a0, u128_sq((uint64_t)(d0 < 0 ? -d0 : d0)));
-            a1 = u128_add(a1, u128_sq((uint64_t)(d1 < 0 ? -d1 : d1)));
+    for (int e0 = 0; e0 < m; e0 += 4) {
+        const int g = min(4, m - e0);
+        int ii[4], jj[4];
+        int64_t ni[4], nj[4];
+        const int64_t *Si[4], *Sj[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            const int idx = first + (e0 + min(u, g - 1)) * stride;
+            ii[u] = pi[idx];
+            jj[u] = pj[idx];
+            Si[u] = L.S + (ro + ii[u]) * L.Bs;
+            Sj[u] = L.S + (ro + jj[u]) * L.Bs;
+            ni[u] = L.n[ro + ii[u]];
+            nj[u] = L.n[ro + jj[u]];
         }
-        a0 = warp_sum_u128(a0);
-        a1 = warp_sum_u128(a1);
-        if (lane == e) { mine = a0; ni_m = ni0; nj_m = nj0; }
-        if (lane == e + 1) { mine = a1; ni_m = ni1; nj_m = nj1; }
-    }
-    if (e < m) {
-        const int i0 = pi[base + e], j0 = pj[base + e];
-        const int64_t *S0 = L.S + (ro + i0) * L.Bs, *T0 = L.S + (ro + j0) * L.Bs;
-        const int64_t ni0 = L.n[ro + i0], nj0 = L.n[ro + j0];
-        u128 a0 = {0, 0};
+        u128 acc[4] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
         for (int b = lane; b < L.B; b += 32) {
-            int64_t d0 = nj0 * S0[b] - ni0 * T0[b];
-            a0 = u128_add(a0, u128_sq((uint64_t)(d0 < 0 ? -d0 : d0)));
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                const int64_t d = nj[u] * Si[u][b] - ni[u] * Sj[u][b];
+                acc[u] = u128_add(acc[u], u128_sq((uint64_t)(d < 0 ? -d : d)));
+            }
         }
-        a0 = warp_sum_u128(a0);
-        if (lane == e) { mine = a0; ni_m = ni0; nj_m = nj0; }
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            const u128 t = warp_sum_u128(acc[u]);
+            if (u < g && lane == e0 + u) { mine = t; ni_m = ni[u]; nj_m = nj[u]; }
+        }
     }
     if (lane < m) {
         u128 D = u128_mul64((uint64_t)ni_m * (uint64_t)nj_m, (uint64_t)(ni_m + nj_m));
-        pkey[base + lane] = dbits(div_rn_u128(mine, D, L.err));
+        pkey[first + lane * stride] = dbits(div_rn_u128(mine, D, L.err));
     }
+}
+
+// All keys of a list of cnt pairs by the whole block (warps round-robin).
+__device__ __forceinline__ void block_keys(const LevelDev &L, int64_t ro, const int32_t *pi, const int32_t *pj,
+                                           unsigned long long *pkey, int cnt)
+{
+    const int wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int base = 0; base < cnt; base += 32 * nw) warp_keys_batch(L, ro, pi, pj, pkey, base + wid, nw, cnt);
 }
 
 __device__ __forceinline__ void set_best(const LevelDev &L, int64_t ro, int r, unsigned long long K,
@@ -582,7 +590,7 @@ __device__ void block_merge(const LevelDev &L, int sec, SecState &st, int a, int
     uint32_t *A = L.adj + L.aoff[sec];
     uint32_t *rowA = A + (int64_t)a * W;
     uint32_t *rowB = A + (int64_t)b * W;
-    const int tid = threadIdx.x, nt = blockDim.x, wid = tid >> 5, nw = nt >> 5;
+    const int tid = threadIdx.x, nt = blockDim.x, wid = tid >> 5;
     const int ab = (rowA[b >> 5] >> (b & 31)) & 1;
     long long pa = 0, pb = 0;
     for (int w = tid; w < W; w += nt) { pa += __popc(rowA[w]); pb += __popc(rowB[w]); }
@@ -690,7 +698,7 @@ __device__ void block_merge(const LevelDev &L, int sec, SecState &st, int a, int
     } else {
         const int np = sm.npair, nr = sm.nrows;
         for (int k = tid; k < nr; k += nt) { sm.rowK[k] = RHSEG_KEY_NONE; sm.rowT[k] = ~0ull; }
-        for (int base = wid * 32; base < np; base += nw * 32) warp_keys_batch(L, ro, sm.pi, sm.pj, sm.pkey, base, np);
+        block_keys(L, ro, sm.pi, sm.pj, sm.pkey, np);
         __syncthreads();
         for (int e = tid; e < np; e += nt) atomicMin(&sm.rowK[sm.prow[e]], sm.pkey[e]);
         __syncthreads();
@@ -887,7 +895,7 @@ __global__ void __launch_bounds__(STEP_THREADS, 2) k_spec_step(LevelDev L, Scree
             }
             __syncthreads();
             const int np = sm.npair;
-            for (int base = wid * 32; base < np; base += nw * 32) warp_keys_batch(L, ro, sm.pi, sm.pj, sm.pkey, base, np);
+            block_keys(L, ro, sm.pi, sm.pj, sm.pkey, np);
             __syncthreads();
             for (int e = tid; e < np; e += nt) {
                 const uint64_t kb = sm.pkey[e];
@@ -936,7 +944,8 @@ __global__ void __launch_bounds__(STEP_THREADS, 2) k_spec_step(LevelDev L, Scree
         if (st.count <= st.target) st.done = 1;
     }
     __syncthreads();
-    if (!st.done && st.count <= (st.mc * 7) / 8 && st.mc > 128) block_compact_positions(L, sec, st);
+    // the screen's work depends on the number of 128-position blocks only
+    if (!st.done && (st.count + 127) / 128 < (st.mc + 127) / 128) block_compact_positions(L, sec, st);
     __syncthreads();
     if (tid == 0) L.st[sec] = st;
 }
