@@ -299,7 +299,7 @@ static size_t op_size(int precision)
 
 static int bpad_for(int precision, int B)
 {
-    if (precision == 1 || precision == 2) return ((B + 63) / 64) * 64;   // 128-byte K atoms
+    if (precision == 1 || precision == 2) return ((B + 31) / 32) * 32;   // 64-byte K atoms of the screen
     return ((B + 15) / 16) * 16;
 }
 

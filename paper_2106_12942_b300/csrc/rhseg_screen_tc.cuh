@@ -11,8 +11,9 @@
 // error bound behind h).  The N^2 matrix is never stored: passing pairs are
 // appended to the section's candidate list for the exact re-check.
 //
-// Roles (192 threads): warp 0 issues TMA loads of 128x64 operand boxes
-// (128-byte swizzle) into a 3-stage shared-memory ring; warp 1 owns the
+// Roles (192 threads): warp 0 issues TMA loads of 128x32 operand boxes
+// (64-byte swizzle, two per operand per stage, so K pads only to 32) into a
+// 3-stage shared-memory ring; warp 1 owns the
 // tensor memory (2 accumulators x 128 columns) and issues tcgen05.mma
 // (M=128, N=128, K=16) from one thread; warps 2-5 read the accumulator with
 // tcgen05.ld (32 lanes each) and run the test.  Persistent CTAs walk the
@@ -28,9 +29,11 @@
 namespace rhseg {
 
 constexpr int TC_TILE = 128;
-constexpr int TC_KATOM = 64;                  // fp16 elements per 128-byte swizzle row
+constexpr int TC_KATOM = 32;                  // 16-bit elements per 64-byte swizzle row (one TMA box)
+constexpr int TC_ATOM_BYTES = TC_TILE * TC_KATOM * 2;        // 8 KB: 128 rows x 64 bytes
+constexpr int TC_ATOMS_PER_STAGE = 2;                        // K = 64 per pipeline stage
 constexpr int TC_STAGES = 3;
-constexpr int TC_STAGE_BYTES = 2 * TC_TILE * TC_KATOM * 2;   // A + B boxes
+constexpr int TC_STAGE_BYTES = 2 * TC_ATOMS_PER_STAGE * TC_ATOM_BYTES;   // A + B
 constexpr int TC_THREADS = 192;
 constexpr long long TC_WAIT_CYCLES = 4000000000ll;           // about 2 s at 2 GHz
 struct TcShared {
@@ -123,16 +126,16 @@ __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, i
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, rows
-// of 128 bytes in groups of 8 (1024-byte stride between groups).
-__device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr)
+// Shared-memory matrix descriptor: K-major operand, 64-byte swizzle, rows
+// of 64 bytes in groups of 8 (512-byte stride between groups).
+__device__ __forceinline__ uint64_t sdesc_sw64(uint32_t saddr)
 {
     uint64_t d = 0;
     d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);       // start address
     d |= (uint64_t)1 << 16;                          // leading offset (unused with this swizzle)
-    d |= (uint64_t)(1024 >> 4) << 32;                // stride offset between 8-row groups
+    d |= (uint64_t)(512 >> 4) << 32;                 // stride offset between 8-row groups
     d |= (uint64_t)1 << 46;                          // descriptor version
-    d |= (uint64_t)2 << 61;                          // 128-byte swizzle
+    d |= (uint64_t)4 << 61;                          // 64-byte swizzle
     return d;
 }
 
@@ -226,7 +229,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_screen_tc(LevelDev L, const _
     uint8_t *ring = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     TcShared &sh = *(TcShared *)(ring + TC_STAGES * TC_STAGE_BYTES);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int nk = L.Bpad / TC_KATOM;
+    const int natoms = L.Bpad / TC_KATOM;                       // 32-element K atoms
+    const int nk = (natoms + TC_ATOMS_PER_STAGE - 1) / TC_ATOMS_PER_STAGE;   // pipeline stages per tile
 
     long long total;
     if (job.gram_rows > 0) {
@@ -269,11 +273,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_screen_tc(LevelDev L, const _
                 if (!tc_tile(L, job, sh.pre, t, total, sec, I, J, rowA, rowB)) break;
                 for (int kc = 0; kc < nk; kc++) {
                     if (!mbar_wait(&sh.empty[stage], phase ^ 1, abort, L.err)) break;
-                    uint8_t *a = ring + stage * TC_STAGE_BYTES;
-                    uint8_t *b = a + TC_TILE * TC_KATOM * 2;
-                    mbar_expect_tx(&sh.full[stage], TC_STAGE_BYTES);
-                    tma_load_2d(a, &tmap, kc * TC_KATOM, (int)rowA, &sh.full[stage], pol);
-                    tma_load_2d(b, &tmap, kc * TC_KATOM, (int)rowB, &sh.full[stage], pol);
+                    uint8_t *a = ring + stage * TC_STAGE_BYTES;                  // A atoms, then B atoms
+                    uint8_t *b = a + TC_ATOMS_PER_STAGE * TC_ATOM_BYTES;
+                    const int na = min(TC_ATOMS_PER_STAGE, natoms - kc * TC_ATOMS_PER_STAGE);
+                    mbar_expect_tx(&sh.full[stage], (uint32_t)(2 * na * TC_ATOM_BYTES));
+                    for (int u = 0; u < na; u++) {
+                        const int x = (kc * TC_ATOMS_PER_STAGE + u) * TC_KATOM;
+                        tma_load_2d(a + u * TC_ATOM_BYTES, &tmap, x, (int)rowA, &sh.full[stage], pol);
+                        tma_load_2d(b + u * TC_ATOM_BYTES, &tmap, x, (int)rowB, &sh.full[stage], pol);
+                    }
                     if (++stage == TC_STAGES) { stage = 0; phase ^= 1; }
                 }
             }
@@ -298,12 +306,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_screen_tc(LevelDev L, const _
                 for (int kc = 0; kc < nk; kc++) {
                     if (!mbar_wait(&sh.full[stage], phase, abort, L.err)) { ok = false; break; }
                     tc_fence_after();
-                    uint32_t a = smem_u32(ring + stage * TC_STAGE_BYTES);
-                    uint32_t b = a + TC_TILE * TC_KATOM * 2;
-                    uint64_t ad = sdesc_sw128(a), bd = sdesc_sw128(b);
+                    const uint32_t a = smem_u32(ring + stage * TC_STAGE_BYTES);
+                    const uint32_t b = a + TC_ATOMS_PER_STAGE * TC_ATOM_BYTES;
+                    const int na = min(TC_ATOMS_PER_STAGE, natoms - kc * TC_ATOMS_PER_STAGE);
+                    for (int u = 0; u < na; u++) {
+                        const uint64_t ad = sdesc_sw64(a + u * TC_ATOM_BYTES), bd = sdesc_sw64(b + u * TC_ATOM_BYTES);
 #pragma unroll
-                    for (int k = 0; k < TC_KATOM / 16; k++)
-                        tc_mma(dt, ad + (uint64_t)(2 * k), bd + (uint64_t)(2 * k), idesc, (kc > 0 || k > 0) ? 1u : 0u);
+                        for (int k = 0; k < TC_KATOM / 16; k++)
+                            tc_mma(dt, ad + (uint64_t)(2 * k), bd + (uint64_t)(2 * k), idesc,
+                                   (kc > 0 || u > 0 || k > 0) ? 1u : 0u);
+                    }
                     tc_commit(&sh.empty[stage]);
                     if (++stage == TC_STAGES) { stage = 0; phase ^= 1; }
                 }
@@ -421,7 +433,7 @@ inline PFN_encodeTiled get_encode_tiled()
     return fn;
 }
 
-// Tensor map over X [rows][Bpad] of 16-bit elements, box 128 rows x 64.
+// Tensor map over X [rows][Bpad] of 16-bit elements, box 128 rows x 32.
 inline int make_operand_map(CUtensorMap *map, const void *X, int64_t rows, int Bpad, int precision)
 {
     PFN_encodeTiled enc = get_encode_tiled();
@@ -433,7 +445,7 @@ inline int make_operand_map(CUtensorMap *map, const void *X, int64_t rows, int B
     cuuint32_t estr[2] = {1, 1};
     CUresult r = enc(map, precision == 2 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2,
                      const_cast<void *>(X), gdim, gstride, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                     CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS ? 0 : -3;
 }

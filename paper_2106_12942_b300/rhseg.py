@@ -183,7 +183,7 @@ def div_rn(n_hi, n_lo, d_hi, d_lo, stream=None):
 def gram_tc(X, precision=1, stream=None):
     """G = X X^T (FP32) of 16-bit rows on the tensor cores (diagnostic of the
     screen's contraction).  X: CUDA tensor float16/bfloat16 [rows, Bpad],
-    rows % 128 == 0, Bpad % 64 == 0."""
+    rows % 128 == 0, Bpad % 32 == 0."""
     import torch
     L = _abi.load()
     X = X.contiguous()

@@ -22,7 +22,7 @@ def P():
 
 
 @pytest.mark.parametrize("precision", [1, 2])
-@pytest.mark.parametrize("rows,bpad", [(128, 64), (256, 128), (384, 256), (128, 448)])
+@pytest.mark.parametrize("rows,bpad", [(128, 64), (256, 128), (384, 256), (128, 448), (256, 224), (128, 32), (256, 96)])
 def test_gram_matches_exact_product(P, precision, rows, bpad):
     import torch
     rng = np.random.default_rng(rows * 7 + bpad + precision)
@@ -49,3 +49,5 @@ def test_gram_rejects_bad_shapes(P):
         P.gram_tc(torch.zeros(100, 64, dtype=torch.float16, device="cuda"))
     with pytest.raises(P.RHSEGError):
         P.gram_tc(torch.zeros(128, 40, dtype=torch.float16, device="cuda"))
+    with pytest.raises(P.RHSEGError):
+        P.gram_tc(torch.zeros(128, 48, dtype=torch.float16, device="cuda"))
