@@ -176,6 +176,19 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32])
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+__device__ __forceinline__ void tmem_ld32_nowait(uint32_t taddr, uint32_t *r)
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+}
+
 // Tile enumeration shared by all roles.  Screen mode: upper-triangle tiles
 // of every section with a pending spectral step and a finite threshold.
 // Gram mode (diagnostic): every (I, J) tile of one block of `gram_rows`.
@@ -366,28 +379,35 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_screen_tc(LevelDev L, const _
             if (!ok) continue;                               // the next loop top stops every warp
             tc_fence_after();
             const uint32_t taddr = tbase + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * TC_TILE);
-            if (job.gram_rows > 0) {
-                for (int c0 = 0; c0 < TC_TILE; c0 += 32) {
-                    uint32_t r[32];
-                    tmem_ld32(taddr + (uint32_t)c0, r);
-                    float *o = job.gram_out + ((int64_t)I * TC_TILE + row) * job.gram_rows + (int64_t)J * TC_TILE + c0;
-#pragma unroll
-                    for (int c = 0; c < 32; c++) o[c] = __uint_as_float(r[c]);
+            const bool diag = (I == J);
+            const float *hcs = sh.hc[buf];
+            SecState *st = (job.gram_rows == 0) ? &L.st[sec] : nullptr;
+            // two halves of 64 columns: two loads, one wait each; the
+            // accumulator is released once the second half is in registers
+            for (int h = 0; h < 2; h++) {
+                uint32_t r[64];
+                tmem_ld32_nowait(taddr + (uint32_t)(h * 64), r);
+                tmem_ld32_nowait(taddr + (uint32_t)(h * 64 + 32), r + 32);
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                if (h == 1) {
+                    tc_fence_before();
+                    mbar_arrive(&sh.tempty[buf]);
                 }
-            } else {
-                SecState *st = &L.st[sec];
-                const bool diag = (I == J);
-                const float *hcs = sh.hc[buf];
-                for (int c0 = 0; c0 < TC_TILE; c0 += 32) {
-                    uint32_t r[32];
-                    tmem_ld32(taddr + (uint32_t)c0, r);
+                if (job.gram_rows > 0) {
+                    float *o = job.gram_out + ((int64_t)I * TC_TILE + row) * job.gram_rows + (int64_t)J * TC_TILE + h * 64;
+#pragma unroll
+                    for (int c = 0; c < 64; c++) o[c] = __uint_as_float(r[c]);
+                    continue;
+                }
+#pragma unroll
+                for (int c0 = 0; c0 < 64; c0 += 32) {
                     float m = -inf;
 #pragma unroll
-                    for (int c = 0; c < 32; c++) m = fmaxf(m, __uint_as_float(r[c]) - hcs[c0 + c]);
+                    for (int c = 0; c < 32; c++) m = fmaxf(m, __uint_as_float(r[c0 + c]) - hcs[h * 64 + c0 + c]);
                     if (m > hr) {
                         for (int c = 0; c < 32; c++) {
-                            int cc = c0 + c;
-                            if (!(__uint_as_float(r[c]) - hcs[cc] > hr)) continue;
+                            const int cc = h * 64 + c0 + c;
+                            if (!(__uint_as_float(r[c0 + c]) - hcs[cc] > hr)) continue;
                             if (diag && cc <= row) continue;
                             uint32_t idx = atomicAdd(&st->ncand, 1u);
                             if ((int64_t)idx < L.cand_cap) {
@@ -399,10 +419,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_screen_tc(LevelDev L, const _
                     }
                 }
             }
-            tc_fence_before();
-            mbar_arrive(&sh.tempty[buf]);
         }
     }
+
     tc_fence_before();
     __syncthreads();
     if (warp == 1) {
