@@ -254,7 +254,7 @@ static int build_geometry(rhseg_handle *h)
             G.area[s] = area;
             G.roff[s] = ro; G.poff[s] = po; G.loff[s] = lo;
             ro += area;
-            po += ((area + 127) / 128) * 128;
+            po += ((area + 255) / 256) * 256;           // whole 256-row operand blocks
             lo += area + 2 * (hh + ww) + 8;
         }
         G.roff[G.nsec] = ro; G.poff[G.nsec] = po; G.loff[G.nsec] = lo;
@@ -1198,13 +1198,13 @@ extern "C" int rhseg_gram_tc(const void *X, int32_t rows, int32_t Bpad, int32_t 
     L.Bpad = Bpad;
     L.nsec = 1;
     TcJob job{rows, G};
-    int nb = rows / TC_TILE;
+    const int units = (rows / TC_TILE) * ((rows + TC_N - 1) / TC_N);
     int nsm = 148;
     {
         int dev = 0;
         if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     }
-    CK(launch_screen_tc_map(L, map, precision, std::max(1, std::min(nb * nb, 2 * nsm) / 2), (cudaStream_t)cuda_stream, job));
+    CK(launch_screen_tc_map(L, map, precision, std::max(1, std::min(units, nsm)), (cudaStream_t)cuda_stream, job));
     return RHSEG_OK;
 }
 

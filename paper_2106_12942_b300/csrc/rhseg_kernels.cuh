@@ -841,7 +841,7 @@ __global__ void __launch_bounds__(STEP_THREADS, 2) k_adj_step(LevelDev L, Screen
     if (L.H != nullptr && st.spec_pending) {
         const float Tf = __double2float_ru(st.tthr);
         const int mc = st.mc;
-        const int pend = ((mc + 127) / 128) * 128;
+        const int pend = ((mc + 255) / 256) * 256;      // the screen reads 256-row column blocks
         const int64_t pb = L.poff[sec];
         const float inf = __int_as_float(0x7f800000);
         for (int pos = threadIdx.x; pos < pend; pos += blockDim.x)

@@ -18,12 +18,23 @@ constexpr int SIMT_TILE = 64;
 constexpr int SIMT_KC = 16;
 constexpr int MAX_SECTIONS = 1024;
 
+// Work units of the tensor-core screen for a section of mc positions:
+// 128-row blocks I against 256-row blocks Jp with 2*Jp + 1 >= I, i.e. the
+// two 128-row halves of every upper-triangle tile of 256-row blocks, less
+// the half past the last row block when the number of 128-row blocks is odd.
+__host__ __device__ __forceinline__ long long tc_section_units(long long mc)
+{
+    const long long nb = (mc + 127) / 128, nbp = (nb + 1) / 2;
+    return nbp * (nbp + 1) - (nb & 1);
+}
+
 // Exclusive prefix over sections of the number of upper-triangle tiles of
-// each pending section (tile edge `tile`).  Whole block; result in pre[0..nsec].
+// each pending section (tile edge `tile`; tile == 0 counts the tensor-core
+// screen's units instead).  Whole block; result in pre[0..nsec].
 __device__ void block_tile_prefix(const LevelDev &L, int tile, long long *pre)
 {
     int nsec = L.nsec;
-    int per = (nsec + blockDim.x - 1) / blockDim.x;      // <= 4 (nsec <= 1024, 256 threads)
+    int per = (nsec + blockDim.x - 1) / blockDim.x;      // <= 16 (nsec <= 1024, >= 64 threads)
     int s0 = threadIdx.x * per;
     long long cnt[16];
     long long loc = 0;
@@ -34,8 +45,12 @@ __device__ void block_tile_prefix(const LevelDev &L, int tile, long long *pre)
         if (k < per && s < nsec) {
             const SecState &st = L.st[s];
             if (st.spec_pending && st.tthr < __longlong_as_double(0x7FF0000000000000ll)) {
-                long long nb = (st.mc + tile - 1) / tile;
-                t = nb * (nb + 1) / 2;
+                if (tile == 0) {
+                    t = tc_section_units(st.mc);
+                } else {
+                    long long nb = (st.mc + tile - 1) / tile;
+                    t = nb * (nb + 1) / 2;
+                }
             }
         }
         cnt[k] = t;

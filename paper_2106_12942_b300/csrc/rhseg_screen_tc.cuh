@@ -4,22 +4,26 @@
 // The all-pairs part of HSEG step 3 (Section 4.1; the thesis's "spectral
 // kernel", Fig. 4.8, evaluates every region pair each iteration) is written
 // as a dense contraction: for region-mean rows x_i (FP16 or BF16, relative
-// to a per-section reference spectrum) the Gram block G = X_I X_J^T of two
-// 128-row blocks is accumulated in FP32 in tensor memory, and the epilogue
-// applies the separable test g_ij > h_i + h_j that keeps every pair whose
-// exact key could be below the step's threshold (see warp_write_row for the
-// error bound behind h).  The N^2 matrix is never stored: passing pairs are
-// appended to the section's candidate list for the exact re-check.
+// to a per-section reference spectrum) the Gram block G = X_I X_J^T of a
+// 128-row block I against a 256-row block Jp is accumulated in FP32 in
+// tensor memory, and the epilogue applies the separable test
+// g_ij > h_i + h_j that keeps every pair whose exact key could be below the
+// step's threshold (see warp_write_row for the error bound behind h).  The
+// N^2 matrix is never stored: passing pairs are appended to the section's
+// candidate list for the exact re-check.
 //
-// Roles (192 threads): warp 0 issues TMA loads of 128x32 operand boxes
-// (64-byte swizzle, two per operand per stage, so K pads only to 32) into a
-// 3-stage shared-memory ring; warp 1 owns the
-// tensor memory (2 accumulators x 128 columns) and issues tcgen05.mma
-// (M=128, N=128, K=16) from one thread; warps 2-5 read the accumulator with
-// tcgen05.ld (32 lanes each) and run the test.  Persistent CTAs walk the
-// upper-triangle tiles of every pending section.  Every mbarrier wait is
-// bounded; a wait that gives up sets the device error word and all roles
-// leave their loops, so the tensor memory is always released.
+// Roles (320 threads, one CTA per SM): warp 0 issues TMA loads of one
+// 32-element K slice per pipeline stage (a 128x32 box of A, two of B;
+// 64-byte swizzle, so K pads only to 32) into an 8-stage shared-memory ring
+// (192 KB in flight); warp 1 owns the tensor memory (2 accumulators x 256
+// columns) and issues tcgen05.mma (M=128, N=256, K=16) from one thread;
+// warps 2-9 read the accumulator with tcgen05.ld (two warps per 32-lane
+// quarter, 128 columns each) and run the test.  The 128x256 unit carries a
+// third more MMA work per operand byte than a 128x128 tile, which is what
+// the screen is bound by: the operand stream from L2.  Persistent CTAs walk
+// the work units of every pending section.  Every mbarrier wait is bounded;
+// a wait that gives up sets the device error word and all roles leave their
+// loops, so the tensor memory is always released.
 #pragma once
 #include <cuda.h>
 #include <cuda_fp16.h>
@@ -28,33 +32,40 @@
 
 namespace rhseg {
 
-constexpr int TC_TILE = 128;
+constexpr int TC_TILE = 128;                  // rows of an A block (M)
+constexpr int TC_N = 256;                     // rows of a B block (N)
 constexpr int TC_KATOM = 32;                  // 16-bit elements per 64-byte swizzle row (one TMA box)
-constexpr int TC_ATOM_BYTES = TC_TILE * TC_KATOM * 2;        // 8 KB: 128 rows x 64 bytes
-constexpr int TC_ATOMS_PER_STAGE = 2;                        // K = 64 per pipeline stage
-constexpr int TC_STAGES = 3;
-constexpr int TC_STAGE_BYTES = 2 * TC_ATOMS_PER_STAGE * TC_ATOM_BYTES;   // A + B
-constexpr int TC_THREADS = 192;
+constexpr int TC_A_BYTES = TC_TILE * TC_KATOM * 2;           // 8 KB: 128 rows x 64 bytes
+constexpr int TC_B_BYTES = TC_N * TC_KATOM * 2;              // 16 KB: 256 rows x 64 bytes
+constexpr int TC_STAGE_BYTES = TC_A_BYTES + TC_B_BYTES;      // one K slice of 32
+constexpr int TC_STAGES = 8;
+constexpr int TC_EPI_WARPS = 8;
+constexpr int TC_THREADS = 64 + 32 * TC_EPI_WARPS;
+constexpr uint32_t TC_TMEM_COLS = 2 * TC_N;
 constexpr long long TC_WAIT_CYCLES = 4000000000ll;           // about 2 s at 2 GHz
 struct TcShared {
     uint64_t full[TC_STAGES], empty[TC_STAGES];
     uint64_t tfull[2], tempty[2];
     uint32_t tmem_base;
     int abort;
-    alignas(16) float hc[2][TC_TILE];
+    alignas(16) float hc[2][TC_N];
     long long pre[MAX_SECTIONS + 1];
+    int smc[MAX_SECTIONS];                    // per section: positions this step
+    int spoff[MAX_SECTIONS];                  // per section: first operand row
 };
 constexpr int TC_SMEM_BYTES = TC_STAGES * TC_STAGE_BYTES + 1024 + (int)((sizeof(TcShared) + 127) / 128 * 128);
+static_assert(TC_SMEM_BYTES <= 227 * 1024, "screen shared memory");
+static_assert(TC_SMEM_BYTES > 227 * 1024 / 2, "one CTA per SM: the tensor memory is allocated whole");
 
-// Barrier 1 over the 128 epilogue threads with an OR-reduction of `v`:
-// every participant gets the same answer.
+// Barrier 1 over the epilogue threads with an OR-reduction of `v`: every
+// participant gets the same answer.
 __device__ __forceinline__ bool epi_bar_or(bool v)
 {
     uint32_t out;
     asm volatile(
         "{\n\t.reg .pred q, p;\n\t"
         "setp.ne.u32 q, %1, 0;\n\t"
-        "bar.red.or.pred p, 1, 128, q;\n\t"
+        "bar.red.or.pred p, 1, 256, q;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}"
         : "=r"(out)
         : "r"((uint32_t)v)
@@ -140,10 +151,10 @@ __device__ __forceinline__ uint64_t sdesc_sw64(uint32_t saddr)
 }
 
 // Instruction descriptor, kind::f16: FP32 accumulator, A/B in FP16 (fmt 0)
-// or BF16 (fmt 1), both K-major, M = N = 128.
+// or BF16 (fmt 1), both K-major, M = 128, N = 256.
 __host__ __device__ constexpr uint32_t idesc_f16(uint32_t fmt)
 {
-    return (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(TC_TILE >> 3) << 17) | ((uint32_t)(TC_TILE >> 4) << 24);
+    return (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(TC_N >> 3) << 17) | ((uint32_t)(TC_TILE >> 4) << 24);
 }
 
 __device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t acc)
@@ -189,48 +200,82 @@ __device__ __forceinline__ void tmem_ld32_nowait(uint32_t taddr, uint32_t *r)
         : "r"(taddr));
 }
 
-// Tile enumeration shared by all roles.  Screen mode: upper-triangle tiles
-// of every section with a pending spectral step and a finite threshold.
-// Gram mode (diagnostic): every (I, J) tile of one block of `gram_rows`.
+// Three-input maximum and a packed pair difference (both exact IEEE
+// operations: max, and subtraction rounded to nearest, lane by lane).
+__device__ __forceinline__ float max3f(float a, float b, float c)
+{
+    float r;
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
+__device__ __forceinline__ void sub2f(float a0, float a1, float b0, float b1, float &d0, float &d1)
+{
+    asm("{\n\t.reg .b64 a, b, d;\n\t"
+        "mov.b64 a, {%2, %3};\n\t"
+        "mov.b64 b, {%4, %5};\n\t"
+        "sub.rn.f32x2 d, a, b;\n\t"
+        "mov.b64 {%0, %1}, d;\n\t}"
+        : "=f"(d0), "=f"(d1)
+        : "f"(a0), "f"(a1), "f"(b0), "f"(b1));
+}
+
+// Work-unit enumeration shared by all roles.  Screen mode: the units of
+// every section with a pending spectral step and a finite threshold (see
+// tc_section_units; unit u of a section is half u & 1 of upper-triangle
+// tile u >> 1 of its 256-row blocks).  Gram mode (diagnostic): every
+// (I, Jp) unit of one block of `gram_rows`.
 struct TcJob {
     int gram_rows;            // > 0: Gram mode
     float *gram_out;          // [gram_rows][gram_rows]
 };
 
-__device__ __forceinline__ bool tc_tile(const LevelDev &L, const TcJob &job, const long long *pre, long long t,
-                                        long long total, int &sec, int &I, int &J, int64_t &rowA, int64_t &rowB)
+struct TcUnit {
+    int sec, I, Jp;
+    int64_t rowA, rowB;       // first operand row of the A block and of the B block
+};
+
+// Unit t of this launch.  `cursor` is the section of the caller's previous
+// unit (units are visited in increasing order, so the section only moves
+// forward); the per-section data come from shared memory.
+__device__ __forceinline__ bool tc_unit(const TcShared &sh, const TcJob &job, long long t, long long total, int &cursor,
+                                        TcUnit &u)
 {
     if (t >= total) return false;
     if (job.gram_rows > 0) {
-        int nb = job.gram_rows / TC_TILE;
-        sec = 0;
-        I = (int)(t / nb);
-        J = (int)(t % nb);
-        rowA = (int64_t)I * TC_TILE;
-        rowB = (int64_t)J * TC_TILE;
+        const int nbp = (job.gram_rows + TC_N - 1) / TC_N;
+        u.sec = 0;
+        u.I = (int)(t / nbp);
+        u.Jp = (int)(t % nbp);
+        u.rowA = (int64_t)u.I * TC_TILE;
+        u.rowB = (int64_t)u.Jp * TC_N;
         return true;
     }
-    sec = find_section(pre, L.nsec, t);
-    int mc = L.st[sec].mc;
-    long long nb = (mc + TC_TILE - 1) / TC_TILE;
-    tri_decode(t - pre[sec], nb, I, J);
-    rowA = L.poff[sec] + (int64_t)I * TC_TILE;
-    rowB = L.poff[sec] + (int64_t)J * TC_TILE;
+    int s = cursor;
+    while (sh.pre[s + 1] <= t) s++;
+    cursor = s;
+    u.sec = s;
+    const long long local = t - sh.pre[s];
+    const long long nb = (sh.smc[s] + TC_TILE - 1) / TC_TILE, nbp = (nb + 1) / 2;
+    int Ip;
+    tri_decode(local >> 1, nbp, Ip, u.Jp);
+    u.I = 2 * Ip + (int)(local & 1);
+    u.rowA = sh.spoff[s] + (int64_t)u.I * TC_TILE;
+    u.rowB = sh.spoff[s] + (int64_t)u.Jp * TC_N;
     return true;
 }
 
-// tc_tile computed by lane 0 and broadcast to the warp.
-__device__ __forceinline__ bool tc_tile_warp(const LevelDev &L, const TcJob &job, const long long *pre, long long t,
-                                             long long total, int &sec, int &I, int &J, int64_t &rowA, int64_t &rowB)
+// tc_unit computed by lane 0 and broadcast to the warp.
+__device__ __forceinline__ bool tc_unit_warp(const TcShared &sh, const TcJob &job, long long t, long long total,
+                                             int &cursor, TcUnit &u)
 {
     int have = 0;
-    if ((threadIdx.x & 31) == 0) have = tc_tile(L, job, pre, t, total, sec, I, J, rowA, rowB) ? 1 : 0;
+    if ((threadIdx.x & 31) == 0) have = tc_unit(sh, job, t, total, cursor, u) ? 1 : 0;
     have = __shfl_sync(0xffffffffu, have, 0);
-    sec = __shfl_sync(0xffffffffu, sec, 0);
-    I = __shfl_sync(0xffffffffu, I, 0);
-    J = __shfl_sync(0xffffffffu, J, 0);
-    rowA = __shfl_sync(0xffffffffu, rowA, 0);
-    rowB = __shfl_sync(0xffffffffu, rowB, 0);
+    u.sec = __shfl_sync(0xffffffffu, u.sec, 0);
+    u.I = __shfl_sync(0xffffffffu, u.I, 0);
+    u.Jp = __shfl_sync(0xffffffffu, u.Jp, 0);
+    u.rowA = __shfl_sync(0xffffffffu, u.rowA, 0);
+    u.rowB = __shfl_sync(0xffffffffu, u.rowB, 0);
     return have != 0;
 }
 
@@ -242,29 +287,36 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_screen_tc(LevelDev L, const _
     uint8_t *ring = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     TcShared &sh = *(TcShared *)(ring + TC_STAGES * TC_STAGE_BYTES);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int natoms = L.Bpad / TC_KATOM;                       // 32-element K atoms
-    const int nk = (natoms + TC_ATOMS_PER_STAGE - 1) / TC_ATOMS_PER_STAGE;   // pipeline stages per tile
+    const int natoms = L.Bpad / TC_KATOM;                       // K slices (pipeline stages) per unit
 
     long long total;
     if (job.gram_rows > 0) {
-        long long nb = job.gram_rows / TC_TILE;
-        total = nb * nb;
+        total = (long long)(job.gram_rows / TC_TILE) * ((job.gram_rows + TC_N - 1) / TC_N);
     } else {
-        block_tile_prefix(L, TC_TILE, sh.pre);
+        block_tile_prefix(L, 0, sh.pre);
         total = sh.pre[L.nsec];
     }
-    if (blockIdx.x >= total) return;     // uniform: this CTA has no tile
+    if (blockIdx.x >= total) return;     // uniform: this CTA has no unit
+    const long long my_units = (total - blockIdx.x + gridDim.x - 1) / gridDim.x;
+    int cursor0 = 0;
+    if (job.gram_rows == 0) {
+        for (int s = threadIdx.x; s < L.nsec; s += blockDim.x) {
+            sh.smc[s] = L.st[s].mc;
+            sh.spoff[s] = (int)L.poff[s];
+        }
+        cursor0 = find_section(sh.pre, L.nsec, blockIdx.x);
+    }
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < TC_STAGES; s++) { mbar_init(&sh.full[s], 1); mbar_init(&sh.empty[s], 1); }
-        for (int b = 0; b < 2; b++) { mbar_init(&sh.tfull[b], 1); mbar_init(&sh.tempty[b], 4 * 32); }
+        for (int b = 0; b < 2; b++) { mbar_init(&sh.tfull[b], 1); mbar_init(&sh.tempty[b], TC_EPI_WARPS * 32); }
         sh.abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&sh.tmem_base)),
-                     "r"(256)
+                     "r"(TC_TMEM_COLS)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -280,21 +332,19 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_screen_tc(LevelDev L, const _
             int stage = 0;
             uint32_t phase = 0;
             const uint64_t pol = l2_evict_first_policy();
+            int cursor = cursor0;
             for (long long t = blockIdx.x; !*abort; t += gridDim.x) {
-                int sec, I, J;
-                int64_t rowA, rowB;
-                if (!tc_tile(L, job, sh.pre, t, total, sec, I, J, rowA, rowB)) break;
-                for (int kc = 0; kc < nk; kc++) {
+                TcUnit u;
+                if (!tc_unit(sh, job, t, total, cursor, u)) break;
+                for (int kc = 0; kc < natoms; kc++) {
                     if (!mbar_wait(&sh.empty[stage], phase ^ 1, abort, L.err)) break;
-                    uint8_t *a = ring + stage * TC_STAGE_BYTES;                  // A atoms, then B atoms
-                    uint8_t *b = a + TC_ATOMS_PER_STAGE * TC_ATOM_BYTES;
-                    const int na = min(TC_ATOMS_PER_STAGE, natoms - kc * TC_ATOMS_PER_STAGE);
-                    mbar_expect_tx(&sh.full[stage], (uint32_t)(2 * na * TC_ATOM_BYTES));
-                    for (int u = 0; u < na; u++) {
-                        const int x = (kc * TC_ATOMS_PER_STAGE + u) * TC_KATOM;
-                        tma_load_2d(a + u * TC_ATOM_BYTES, &tmap, x, (int)rowA, &sh.full[stage], pol);
-                        tma_load_2d(b + u * TC_ATOM_BYTES, &tmap, x, (int)rowB, &sh.full[stage], pol);
-                    }
+                    uint8_t *a = ring + stage * TC_STAGE_BYTES;                  // A slice, then B slice
+                    uint8_t *b = a + TC_A_BYTES;
+                    const int x = kc * TC_KATOM;
+                    mbar_expect_tx(&sh.full[stage], (uint32_t)TC_STAGE_BYTES);
+                    tma_load_2d(a, &tmap, x, (int)u.rowA, &sh.full[stage], pol);
+                    tma_load_2d(b, &tmap, x, (int)u.rowB, &sh.full[stage], pol);
+                    tma_load_2d(b + TC_A_BYTES, &tmap, x, (int)u.rowB + TC_TILE, &sh.full[stage], pol);
                     if (++stage == TC_STAGES) { stage = 0; phase ^= 1; }
                 }
             }
@@ -307,28 +357,20 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_screen_tc(LevelDev L, const _
             int stage = 0;
             uint32_t phase = 0;
             int tcount = 0;
-            for (long long t = blockIdx.x; !*abort; t += gridDim.x, tcount++) {
-                int sec, I, J;
-                int64_t rowA, rowB;
-                if (!tc_tile(L, job, sh.pre, t, total, sec, I, J, rowA, rowB)) break;
-                int buf = tcount & 1;
+            for (; tcount < my_units && !*abort; tcount++) {
+                const int buf = tcount & 1;
                 if (!mbar_wait(&sh.tempty[buf], ((tcount >> 1) & 1) ^ 1, abort, L.err)) break;
                 tc_fence_after();
-                uint32_t dt = tbase + (uint32_t)(buf * TC_TILE);
+                const uint32_t dt = tbase + (uint32_t)(buf * TC_N);
                 bool ok = true;
-                for (int kc = 0; kc < nk; kc++) {
+                for (int kc = 0; kc < natoms; kc++) {
                     if (!mbar_wait(&sh.full[stage], phase, abort, L.err)) { ok = false; break; }
                     tc_fence_after();
                     const uint32_t a = smem_u32(ring + stage * TC_STAGE_BYTES);
-                    const uint32_t b = a + TC_ATOMS_PER_STAGE * TC_ATOM_BYTES;
-                    const int na = min(TC_ATOMS_PER_STAGE, natoms - kc * TC_ATOMS_PER_STAGE);
-                    for (int u = 0; u < na; u++) {
-                        const uint64_t ad = sdesc_sw64(a + u * TC_ATOM_BYTES), bd = sdesc_sw64(b + u * TC_ATOM_BYTES);
+                    const uint64_t ad = sdesc_sw64(a), bd = sdesc_sw64(a + TC_A_BYTES);
 #pragma unroll
-                        for (int k = 0; k < TC_KATOM / 16; k++)
-                            tc_mma(dt, ad + (uint64_t)(2 * k), bd + (uint64_t)(2 * k), idesc,
-                                   (kc > 0 || u > 0 || k > 0) ? 1u : 0u);
-                    }
+                    for (int k = 0; k < TC_KATOM / 16; k++)
+                        tc_mma(dt, ad + (uint64_t)(2 * k), bd + (uint64_t)(2 * k), idesc, (kc > 0 || k > 0) ? 1u : 0u);
                     tc_commit(&sh.empty[stage]);
                     if (++stage == TC_STAGES) { stage = 0; phase ^= 1; }
                 }
@@ -338,50 +380,53 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_screen_tc(LevelDev L, const _
         }
         __syncwarp();
     } else {
-        // ---------------- epilogue: warps 2..5 ----------------
-        // Each thread owns one accumulator row (TMEM lane).  The per-row
-        // terms h of the next tile are fetched while the current tile is
+        // ---------------- epilogue: warps 2..9 ----------------
+        // Each thread owns one accumulator row (TMEM lane) and one half of
+        // the 256 columns: 128-row block J = 2 Jp + ch of the unit.  The h
+        // terms of the next unit are fetched while the current one is
         // tested; the test runs as max_j (g_ij - h_j) > h_i over 32 columns
         // and only a passing chunk is examined element by element.
         const int q = warp & 3;                     // tensor-memory lane quarter of this warp
+        const int ch = (warp - 2) >> 2;             // column half
         const int row = q * 32 + lane;              // accumulator row = TMEM lane
-        const int et = threadIdx.x - 64;            // 0..127, column index for h
+        const int et = threadIdx.x - 64;            // 0..255, column index for h
         const float inf = __int_as_float(0x7f800000);
         int tcount = 0;
+        int cursor = cursor0;
         float hc_next = inf, hr_next = inf;
-        {
-            int sec = 0, I = 0, J = 0;
-            int64_t rowA = 0, rowB = 0;
-            if (tc_tile_warp(L, job, sh.pre, blockIdx.x, total, sec, I, J, rowA, rowB) && job.gram_rows == 0) {
-                hc_next = L.H[rowB + et];
-                hr_next = L.H[rowA + row];
-            }
+        TcUnit u;
+        bool have = tc_unit_warp(sh, job, blockIdx.x, total, cursor, u);
+        if (have && job.gram_rows == 0) {
+            hc_next = L.H[u.rowB + et];
+            hr_next = L.H[u.rowA + row];
         }
         for (long long t = blockIdx.x;; t += gridDim.x, tcount++) {
-            int sec = 0, I = 0, J = 0;
-            int64_t rowA = 0, rowB = 0;
-            bool have = tc_tile_warp(L, job, sh.pre, t, total, sec, I, J, rowA, rowB);
-            if (epi_bar_or(!have || *abort)) break;          // uniform over the 128 threads
+            if (epi_bar_or(!have || *abort)) break;          // uniform over the epilogue threads
             const int buf = tcount & 1;
             sh.hc[buf][et] = hc_next;
             const float hr = hr_next;
-            asm volatile("bar.sync 1, 128;" ::: "memory");
-            if (job.gram_rows == 0) {
-                int s2 = 0, I2 = 0, J2 = 0;
-                int64_t rA2 = 0, rB2 = 0;
-                if (tc_tile_warp(L, job, sh.pre, t + gridDim.x, total, s2, I2, J2, rA2, rB2)) {
-                    hc_next = L.H[rB2 + et];
-                    hr_next = L.H[rA2 + row];
-                }
+            asm volatile("bar.sync 1, %0;" ::"n"(TC_EPI_WARPS * 32) : "memory");
+            const TcUnit cur = u;
+            have = tc_unit_warp(sh, job, t + gridDim.x, total, cursor, u);     // the next unit
+            if (have && job.gram_rows == 0) {
+                hc_next = L.H[u.rowB + et];
+                hr_next = L.H[u.rowA + row];
             }
             bool ok = mbar_wait(&sh.tfull[buf], (tcount >> 1) & 1, abort, L.err);
             ok = __all_sync(0xffffffffu, ok);
             if (!ok) continue;                               // the next loop top stops every warp
             tc_fence_after();
-            const uint32_t taddr = tbase + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * TC_TILE);
-            const bool diag = (I == J);
-            const float *hcs = sh.hc[buf];
-            SecState *st = (job.gram_rows == 0) ? &L.st[sec] : nullptr;
+            const int J = 2 * cur.Jp + ch;                     // 128-row block of this thread's columns
+            const bool skip = (job.gram_rows > 0) ? (J * TC_TILE >= job.gram_rows) : (J < cur.I);
+            if (skip) {                                      // past the Gram rows, or a lower-triangle block
+                tc_fence_before();
+                mbar_arrive(&sh.tempty[buf]);
+                continue;
+            }
+            const uint32_t taddr = tbase + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * TC_N + ch * TC_TILE);
+            const bool diag = (J == cur.I);
+            const float *hcs = sh.hc[buf] + ch * TC_TILE;
+            SecState *st = (job.gram_rows == 0) ? &L.st[cur.sec] : nullptr;
             // two halves of 64 columns: two loads, one wait each; the
             // accumulator is released once the second half is in registers
             for (int h = 0; h < 2; h++) {
@@ -394,25 +439,39 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_screen_tc(LevelDev L, const _
                     mbar_arrive(&sh.tempty[buf]);
                 }
                 if (job.gram_rows > 0) {
-                    float *o = job.gram_out + ((int64_t)I * TC_TILE + row) * job.gram_rows + (int64_t)J * TC_TILE + h * 64;
+                    float *o = job.gram_out + ((int64_t)cur.I * TC_TILE + row) * job.gram_rows + (int64_t)J * TC_TILE + h * 64;
 #pragma unroll
                     for (int c = 0; c < 64; c++) o[c] = __uint_as_float(r[c]);
                     continue;
                 }
 #pragma unroll
                 for (int c0 = 0; c0 < 64; c0 += 32) {
-                    float m = -inf;
+                    const float4 *h4 = (const float4 *)(hcs + h * 64 + c0);
+                    float d[32];
 #pragma unroll
-                    for (int c = 0; c < 32; c++) m = fmaxf(m, __uint_as_float(r[c0 + c]) - hcs[h * 64 + c0 + c]);
+                    for (int c = 0; c < 32; c += 4) {
+                        const float4 hv = h4[c / 4];
+                        sub2f(__uint_as_float(r[c0 + c]), __uint_as_float(r[c0 + c + 1]), hv.x, hv.y, d[c], d[c + 1]);
+                        sub2f(__uint_as_float(r[c0 + c + 2]), __uint_as_float(r[c0 + c + 3]), hv.z, hv.w, d[c + 2],
+                              d[c + 3]);
+                    }
+                    float m0 = max3f(d[0], d[1], d[2]), m1 = max3f(d[3], d[4], d[5]);
+                    m0 = max3f(m0, d[6], d[7]);   m1 = max3f(m1, d[8], d[9]);
+                    m0 = max3f(m0, d[10], d[11]); m1 = max3f(m1, d[12], d[13]);
+                    m0 = max3f(m0, d[14], d[15]); m1 = max3f(m1, d[16], d[17]);
+                    m0 = max3f(m0, d[18], d[19]); m1 = max3f(m1, d[20], d[21]);
+                    m0 = max3f(m0, d[22], d[23]); m1 = max3f(m1, d[24], d[25]);
+                    m0 = max3f(m0, d[26], d[27]); m1 = max3f(m1, d[28], d[29]);
+                    const float m = max3f(m0, m1, fmaxf(d[30], d[31]));
                     if (m > hr) {
                         for (int c = 0; c < 32; c++) {
                             const int cc = h * 64 + c0 + c;
-                            if (!(__uint_as_float(r[c0 + c]) - hcs[cc] > hr)) continue;
+                            if (!(d[c] > hr)) continue;
                             if (diag && cc <= row) continue;
                             uint32_t idx = atomicAdd(&st->ncand, 1u);
                             if ((int64_t)idx < L.cand_cap) {
-                                uint32_t *cd = L.cand + ((int64_t)sec * L.cand_cap + idx) * 2;
-                                cd[0] = (uint32_t)(I * TC_TILE + row);
+                                uint32_t *cd = L.cand + ((int64_t)cur.sec * L.cand_cap + idx) * 2;
+                                cd[0] = (uint32_t)(cur.I * TC_TILE + row);
                                 cd[1] = (uint32_t)(J * TC_TILE + cc);
                             }
                         }
@@ -426,7 +485,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_screen_tc(LevelDev L, const _
     __syncthreads();
     if (warp == 1) {
         tc_fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(256) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(TC_TMEM_COLS) : "memory");
     }
 }
 
@@ -471,8 +530,10 @@ inline int make_operand_map(CUtensorMap *map, const void *X, int64_t rows, int B
 
 inline bool screen_uses_tcgen05(int precision) { return precision == 1 || precision == 2; }
 
-// Launch the screen for a level.  `map` must describe L.X.
-inline cudaError_t launch_screen_tc_map(const LevelDev &L, const CUtensorMap &map, int precision, int n_sm,
+// Launch the screen for a level.  `map` must describe L.X.  One persistent
+// CTA per SM (the shared memory admits no second one); `n_cta` caps the
+// grid (the units are dealt out round-robin).
+inline cudaError_t launch_screen_tc_map(const LevelDev &L, const CUtensorMap &map, int precision, int n_cta,
                                         cudaStream_t s, TcJob job)
 {
     static bool attr_done[2] = {false, false};
@@ -486,9 +547,8 @@ inline cudaError_t launch_screen_tc_map(const LevelDev &L, const CUtensorMap &ma
         if (e != cudaSuccess) return e;
         attr_done[fi] = true;
     }
-    // two persistent CTAs per SM (shared memory 106 KB, tensor memory 256 columns each)
-    if (precision == 2) k_screen_tc<1><<<2 * n_sm, TC_THREADS, TC_SMEM_BYTES, s>>>(L, map, job);
-    else k_screen_tc<0><<<2 * n_sm, TC_THREADS, TC_SMEM_BYTES, s>>>(L, map, job);
+    if (precision == 2) k_screen_tc<1><<<n_cta, TC_THREADS, TC_SMEM_BYTES, s>>>(L, map, job);
+    else k_screen_tc<0><<<n_cta, TC_THREADS, TC_SMEM_BYTES, s>>>(L, map, job);
     return cudaGetLastError();
 }
 
