@@ -221,7 +221,8 @@ int rhseg_div_rn(const uint64_t *n_hi, const uint64_t *n_lo, const uint64_t *d_h
 
 /* Diagnostic of the tensor-core screen's contraction: G = X X^T in FP32 for
  * X = [rows][Bpad] FP16 (precision 1) or BF16 (precision 2) device rows,
- * rows a multiple of 128, Bpad a multiple of 32; G [rows][rows] device
+ * rows a multiple of 128, Bpad a multiple of 32 and at most 4096 (else
+ * RHSEG_EINVAL); G [rows][rows] device
  * float.  Uses the same TMA/tcgen05 main loop as the spectral screen
  * (Section 4.2's spectral kernel, here as a Gram contraction).  Does not
  * wait. */

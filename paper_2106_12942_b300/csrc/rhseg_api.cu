@@ -1187,7 +1187,8 @@ __global__ void k_div(const uint64_t *nh, const uint64_t *nl, const uint64_t *dh
 extern "C" int rhseg_gram_tc(const void *X, int32_t rows, int32_t Bpad, int32_t precision, float *G,
                              void *cuda_stream)
 {
-    if (!X || !G || rows <= 0 || rows % TC_TILE || Bpad <= 0 || Bpad % TC_KATOM || (precision != 1 && precision != 2))
+    if (!X || !G || rows <= 0 || rows % TC_TILE || Bpad <= 0 || Bpad % TC_KATOM || Bpad > 4096 ||
+        (precision != 1 && precision != 2))
         return RHSEG_EINVAL;
     CUtensorMap map;
     if (make_operand_map(&map, X, rows, Bpad, precision)) {

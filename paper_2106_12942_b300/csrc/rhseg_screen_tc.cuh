@@ -12,13 +12,15 @@
 // N^2 matrix is never stored: passing pairs are appended to the section's
 // candidate list for the exact re-check.
 //
-// Roles (320 threads, one CTA per SM): warp 0 issues TMA loads of one
+// Roles (416 threads, one CTA per SM): warps 0-3 issue TMA loads of one
 // 32-element K slice per pipeline stage (a 128x32 box of A, two of B;
 // 64-byte swizzle, so K pads only to 32) into an 8-stage shared-memory ring
-// (192 KB in flight); warp 1 owns the tensor memory (2 accumulators x 256
-// columns) and issues tcgen05.mma (M=128, N=256, K=16) from one thread;
-// warps 2-9 read the accumulator with tcgen05.ld (two warps per 32-lane
-// quarter, 128 columns each) and run the test.  The 128x256 unit carries a
+// (192 KB in flight; one TMA-issuing thread per SM delivers only a fraction
+// of what four do); warp 4 owns the tensor memory (2 accumulators x 256
+// columns) and issues tcgen05.mma (M=128, N=256, K=16) from one thread,
+// committing once per group of K slices (each commit costs the tensor pipe
+// about one MMA); warps 5-12 read the accumulator with tcgen05.ld (two
+// warps per 32-lane quarter, 128 columns each) and run the test.  The 128x256 unit carries a
 // third more MMA work per operand byte than a 128x128 tile, which is what
 // the screen is bound by: the operand stream from L2.  Persistent CTAs walk
 // the work units of every pending section.  Every mbarrier wait is bounded;
@@ -39,15 +41,34 @@ constexpr int TC_A_BYTES = TC_TILE * TC_KATOM * 2;           // 8 KB: 128 rows x
 constexpr int TC_B_BYTES = TC_N * TC_KATOM * 2;              // 16 KB: 256 rows x 64 bytes
 constexpr int TC_STAGE_BYTES = TC_A_BYTES + TC_B_BYTES;      // one K slice of 32
 constexpr int TC_STAGES = 8;
+constexpr int TC_GROUP = 4;                   // K slices per tcgen05.commit (a commit costs ~1 MMA of pipe time)
+constexpr int TC_PROD_WARPS = 4;              // TMA issuing warps (one thread each; TMA rate grows with issuers)
+constexpr int TC_NGBAR = 32;                  // group-completion barriers, used round-robin
+constexpr int TC_NDESC = 16;                  // unit descriptors published ahead by the producer
 constexpr int TC_EPI_WARPS = 8;
-constexpr int TC_THREADS = 64 + 32 * TC_EPI_WARPS;
+constexpr int TC_MMA_WARP = TC_PROD_WARPS;
+constexpr int TC_EPI_WARP0 = TC_PROD_WARPS + 1;
+constexpr int TC_THREADS = 32 * (TC_PROD_WARPS + 1 + TC_EPI_WARPS);
+static_assert(TC_STAGES % TC_PROD_WARPS == 0, "each producer owns whole ring slots");
 constexpr uint32_t TC_TMEM_COLS = 2 * TC_N;
 constexpr long long TC_WAIT_CYCLES = 4000000000ll;           // about 2 s at 2 GHz
+
+// One work unit: rows [rowA, rowA + 128) against rows [rowB, rowB + 256).
+struct TcUnit {
+    int sec, I, Jp, pad;
+    int64_t rowA, rowB;
+};
+
 struct TcShared {
-    uint64_t full[TC_STAGES], empty[TC_STAGES];
-    uint64_t tfull[2], tempty[2];
+    uint64_t full[TC_STAGES];                 // K slice landed (TMA transaction count)
+    uint64_t gbar[TC_NGBAR];                  // MMAs of a group of K slices complete
+    uint64_t tempty[2];                       // accumulator buffer read out by the epilogue
+    uint64_t dfull[TC_NDESC], dempty[TC_NDESC];
     uint32_t tmem_base;
     int abort;
+    long long slot_q[TC_STAGES];              // producer only: group that last read each ring slot
+    int slot_fills[TC_STAGES];                // producer only: loads issued into each ring slot
+    TcUnit desc[TC_NDESC];
     alignas(16) float hc[2][TC_N];
     long long pre[MAX_SECTIONS + 1];
     int smc[MAX_SECTIONS];                    // per section: positions this step
@@ -112,6 +133,19 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volati
         }
     }
     return true;
+}
+
+// Bounded wait that ignores the abort flag: used only to let this CTA's own
+// TMA copies land before it exits.
+__device__ __forceinline__ void mbar_wait_landed(uint64_t *bar, uint32_t parity, int32_t *err)
+{
+    long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity)) {
+        if (clock64() - t0 > TC_WAIT_CYCLES) {
+            if (err) atomicExch(err, 0x54434c44);   // copies still in flight at exit
+            return;
+        }
+    }
 }
 
 // L2 policy for the streamed operand rows: evicted before other lines, so
@@ -229,11 +263,6 @@ struct TcJob {
     float *gram_out;          // [gram_rows][gram_rows]
 };
 
-struct TcUnit {
-    int sec, I, Jp;
-    int64_t rowA, rowB;       // first operand row of the A block and of the B block
-};
-
 // Unit t of this launch.  `cursor` is the section of the caller's previous
 // unit (units are visited in increasing order, so the section only moves
 // forward); the per-section data come from shared memory.
@@ -264,21 +293,6 @@ __device__ __forceinline__ bool tc_unit(const TcShared &sh, const TcJob &job, lo
     return true;
 }
 
-// tc_unit computed by lane 0 and broadcast to the warp.
-__device__ __forceinline__ bool tc_unit_warp(const TcShared &sh, const TcJob &job, long long t, long long total,
-                                             int &cursor, TcUnit &u)
-{
-    int have = 0;
-    if ((threadIdx.x & 31) == 0) have = tc_unit(sh, job, t, total, cursor, u) ? 1 : 0;
-    have = __shfl_sync(0xffffffffu, have, 0);
-    u.sec = __shfl_sync(0xffffffffu, u.sec, 0);
-    u.I = __shfl_sync(0xffffffffu, u.I, 0);
-    u.Jp = __shfl_sync(0xffffffffu, u.Jp, 0);
-    u.rowA = __shfl_sync(0xffffffffu, u.rowA, 0);
-    u.rowB = __shfl_sync(0xffffffffu, u.rowB, 0);
-    return have != 0;
-}
-
 template <int FMT>
 __global__ void __launch_bounds__(TC_THREADS, 1) k_screen_tc(LevelDev L, const __grid_constant__ CUtensorMap tmap,
                                                              TcJob job)
@@ -307,14 +321,26 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_screen_tc(LevelDev L, const _
         cursor0 = find_section(sh.pre, L.nsec, blockIdx.x);
     }
 
+    // K slices per commit: TC_GROUP, widened for very wide rows so that a
+    // unit never spans more than 16 groups (the group barriers are reused
+    // after TC_NGBAR groups; the epilogue trails the MMAs by at most one unit)
+    const int G = max(TC_GROUP, (natoms + 15) / 16);
+    const int gpu = (natoms + G - 1) / G;                    // groups per unit
+    if (G > TC_STAGES) {                 // a group must fit the ring (rows of at most 4096 elements)
+        if (threadIdx.x == 0 && L.err) atomicExch(L.err, 0x54434752);
+        return;                          // uniform: before any barrier or tensor-memory use
+    }
+
     if (threadIdx.x == 0) {
-        for (int s = 0; s < TC_STAGES; s++) { mbar_init(&sh.full[s], 1); mbar_init(&sh.empty[s], 1); }
-        for (int b = 0; b < 2; b++) { mbar_init(&sh.tfull[b], 1); mbar_init(&sh.tempty[b], TC_EPI_WARPS * 32); }
+        for (int s = 0; s < TC_STAGES; s++) { mbar_init(&sh.full[s], 1); sh.slot_q[s] = -1; sh.slot_fills[s] = 0; }
+        for (int g = 0; g < TC_NGBAR; g++) mbar_init(&sh.gbar[g], 1);
+        for (int b = 0; b < 2; b++) mbar_init(&sh.tempty[b], TC_EPI_WARPS);
+        for (int d = 0; d < TC_NDESC; d++) { mbar_init(&sh.dfull[d], 1); mbar_init(&sh.dempty[d], TC_EPI_WARPS); }
         sh.abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
-    if (warp == 1) {
+    if (warp == TC_MMA_WARP) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&sh.tmem_base)),
                      "r"(TC_TMEM_COLS)
                      : "memory");
@@ -326,104 +352,140 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_screen_tc(LevelDev L, const _
     const uint32_t tbase = sh.tmem_base;
     volatile int *abort = &sh.abort;
 
-    if (warp == 0) {
-        // ---------------- TMA producer ----------------
+    if (warp < TC_PROD_WARPS) {
+        // ---------------- producers: unit decode + TMA ----------------
+        // Producer p streams the K slices c = p, p + 4, ... of this CTA's
+        // sequence (slot c mod 8, so each producer owns two ring slots); the
+        // producer of a unit's first slice publishes the unit's descriptor
+        // for the epilogue.  A slot is refilled once the commit group that
+        // read it has completed.
         if (lane == 0) {
-            int stage = 0;
-            uint32_t phase = 0;
+            const int p = warp;
             const uint64_t pol = l2_evict_first_policy();
             int cursor = cursor0;
-            for (long long t = blockIdx.x; !*abort; t += gridDim.x) {
-                TcUnit u;
-                if (!tc_unit(sh, job, t, total, cursor, u)) break;
-                for (int kc = 0; kc < natoms; kc++) {
-                    if (!mbar_wait(&sh.empty[stage], phase ^ 1, abort, L.err)) break;
-                    uint8_t *a = ring + stage * TC_STAGE_BYTES;                  // A slice, then B slice
-                    uint8_t *b = a + TC_A_BYTES;
-                    const int x = kc * TC_KATOM;
-                    mbar_expect_tx(&sh.full[stage], (uint32_t)TC_STAGE_BYTES);
-                    tma_load_2d(a, &tmap, x, (int)u.rowA, &sh.full[stage], pol);
-                    tma_load_2d(b, &tmap, x, (int)u.rowB, &sh.full[stage], pol);
-                    tma_load_2d(b + TC_A_BYTES, &tmap, x, (int)u.rowB + TC_TILE, &sh.full[stage], pol);
-                    if (++stage == TC_STAGES) { stage = 0; phase ^= 1; }
+            long long kdec = -1;
+            TcUnit u{};
+            const long long nslices = my_units * natoms;
+            for (long long c = p; c < nslices && !*abort; c += TC_PROD_WARPS) {
+                const long long k = c / natoms;
+                const int kc = (int)(c - k * natoms);
+                const int slot = (int)(c % TC_STAGES);
+                if (k != kdec) {
+                    tc_unit(sh, job, blockIdx.x + k * gridDim.x, total, cursor, u);
+                    kdec = k;
                 }
+                if (kc == 0) {
+                    const int ds = (int)(k % TC_NDESC);
+                    if (k >= TC_NDESC && !mbar_wait(&sh.dempty[ds], (uint32_t)((k / TC_NDESC - 1) & 1), abort, L.err))
+                        break;
+                    sh.desc[ds] = u;
+                    mbar_arrive(&sh.dfull[ds]);
+                }
+                const long long qo = sh.slot_q[slot];
+                if (qo >= 0 && !mbar_wait(&sh.gbar[qo % TC_NGBAR], (uint32_t)((qo / TC_NGBAR) & 1), abort, L.err)) break;
+                uint8_t *a = ring + slot * TC_STAGE_BYTES;                       // A slice, then B slice
+                uint8_t *b = a + TC_A_BYTES;
+                const int x = kc * TC_KATOM;
+                mbar_expect_tx(&sh.full[slot], (uint32_t)TC_STAGE_BYTES);
+                tma_load_2d(a, &tmap, x, (int)u.rowA, &sh.full[slot], pol);
+                tma_load_2d(b, &tmap, x, (int)u.rowB, &sh.full[slot], pol);
+                tma_load_2d(b + TC_A_BYTES, &tmap, x, (int)u.rowB + TC_TILE, &sh.full[slot], pol);
+                sh.slot_q[slot] = k * gpu + kc / G;
+                sh.slot_fills[slot]++;
             }
+            // every load this producer issued has landed before the CTA may
+            // exit (immediate unless the CTA aborted with copies in flight)
+            for (int sl = p; sl < TC_STAGES; sl += TC_PROD_WARPS)
+                if (sh.slot_fills[sl] > 0) mbar_wait_landed(&sh.full[sl], (uint32_t)((sh.slot_fills[sl] - 1) & 1), L.err);
         }
         __syncwarp();
-    } else if (warp == 1) {
+    } else if (warp == TC_MMA_WARP) {
         // ---------------- MMA issuer ----------------
         if (lane == 0) {
             const uint32_t idesc = idesc_f16(FMT);
-            int stage = 0;
+            int slot = 0;
             uint32_t phase = 0;
-            int tcount = 0;
-            for (; tcount < my_units && !*abort; tcount++) {
-                const int buf = tcount & 1;
-                if (!mbar_wait(&sh.tempty[buf], ((tcount >> 1) & 1) ^ 1, abort, L.err)) break;
+            long long q = 0;                                     // commit groups issued
+            for (long long k = 0; k < my_units && !*abort; k++) {
+                const int buf = (int)(k & 1);
+                if (!mbar_wait(&sh.tempty[buf], (uint32_t)(((k >> 1) & 1) ^ 1), abort, L.err)) break;
                 tc_fence_after();
                 const uint32_t dt = tbase + (uint32_t)(buf * TC_N);
                 bool ok = true;
                 for (int kc = 0; kc < natoms; kc++) {
-                    if (!mbar_wait(&sh.full[stage], phase, abort, L.err)) { ok = false; break; }
+                    if (!mbar_wait(&sh.full[slot], phase, abort, L.err)) { ok = false; break; }
                     tc_fence_after();
-                    const uint32_t a = smem_u32(ring + stage * TC_STAGE_BYTES);
+                    const uint32_t a = smem_u32(ring + slot * TC_STAGE_BYTES);
                     const uint64_t ad = sdesc_sw64(a), bd = sdesc_sw64(a + TC_A_BYTES);
 #pragma unroll
-                    for (int k = 0; k < TC_KATOM / 16; k++)
-                        tc_mma(dt, ad + (uint64_t)(2 * k), bd + (uint64_t)(2 * k), idesc, (kc > 0 || k > 0) ? 1u : 0u);
-                    tc_commit(&sh.empty[stage]);
-                    if (++stage == TC_STAGES) { stage = 0; phase ^= 1; }
+                    for (int kk = 0; kk < TC_KATOM / 16; kk++)
+                        tc_mma(dt, ad + (uint64_t)(2 * kk), bd + (uint64_t)(2 * kk), idesc, (kc > 0 || kk > 0) ? 1u : 0u);
+                    if (++slot == TC_STAGES) { slot = 0; phase ^= 1; }
+                    if ((kc + 1) % G == 0 || kc + 1 == natoms) {
+                        tc_commit(&sh.gbar[q % TC_NGBAR]);          // releases the group's slots; the
+                        q++;                                         // unit's last group also readies D
+                    }
                 }
                 if (!ok) break;
-                tc_commit(&sh.tfull[buf]);
             }
         }
         __syncwarp();
     } else {
-        // ---------------- epilogue: warps 2..9 ----------------
+        // ---------------- epilogue: warps 5..12 ----------------
         // Each thread owns one accumulator row (TMEM lane) and one half of
         // the 256 columns: 128-row block J = 2 Jp + ch of the unit.  The h
         // terms of the next unit are fetched while the current one is
         // tested; the test runs as max_j (g_ij - h_j) > h_i over 32 columns
         // and only a passing chunk is examined element by element.
-        const int q = warp & 3;                     // tensor-memory lane quarter of this warp
-        const int ch = (warp - 2) >> 2;             // column half
-        const int row = q * 32 + lane;              // accumulator row = TMEM lane
-        const int et = threadIdx.x - 64;            // 0..255, column index for h
+        const int q4 = warp & 3;                    // tensor-memory lane quarter of this warp
+        const int ch = (warp - TC_EPI_WARP0) >> 2;  // column half
+        const int row = q4 * 32 + lane;             // accumulator row = TMEM lane
+        const int et = threadIdx.x - 32 * TC_EPI_WARP0;   // 0..255, column index for h
         const float inf = __int_as_float(0x7f800000);
-        int tcount = 0;
-        int cursor = cursor0;
         float hc_next = inf, hr_next = inf;
-        TcUnit u;
-        bool have = tc_unit_warp(sh, job, blockIdx.x, total, cursor, u);
-        if (have && job.gram_rows == 0) {
-            hc_next = L.H[u.rowB + et];
-            hr_next = L.H[u.rowA + row];
+        TcUnit nxt{};
+        bool ok0 = mbar_wait(&sh.dfull[0], 0, abort, L.err);
+        if (ok0) {
+            nxt = sh.desc[0];
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&sh.dempty[0]);
+            if (job.gram_rows == 0) {
+                hc_next = L.H[nxt.rowB + et];
+                hr_next = L.H[nxt.rowA + row];
+            }
         }
-        for (long long t = blockIdx.x;; t += gridDim.x, tcount++) {
-            if (epi_bar_or(!have || *abort)) break;          // uniform over the epilogue threads
-            const int buf = tcount & 1;
+        for (long long k = 0; k < my_units; k++) {
+            if (epi_bar_or(*abort != 0)) break;              // uniform over the epilogue threads
+            const int buf = (int)(k & 1);
+            const TcUnit cur = nxt;
             sh.hc[buf][et] = hc_next;
             const float hr = hr_next;
             asm volatile("bar.sync 1, %0;" ::"n"(TC_EPI_WARPS * 32) : "memory");
-            const TcUnit cur = u;
-            have = tc_unit_warp(sh, job, t + gridDim.x, total, cursor, u);     // the next unit
-            if (have && job.gram_rows == 0) {
-                hc_next = L.H[u.rowB + et];
-                hr_next = L.H[u.rowA + row];
+            if (k + 1 < my_units) {
+                const int ds = (int)((k + 1) % TC_NDESC);
+                if (mbar_wait(&sh.dfull[ds], (uint32_t)(((k + 1) / TC_NDESC) & 1), abort, L.err)) {
+                    nxt = sh.desc[ds];
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&sh.dempty[ds]);
+                    if (job.gram_rows == 0) {
+                        hc_next = L.H[nxt.rowB + et];
+                        hr_next = L.H[nxt.rowA + row];
+                    }
+                }
             }
-            bool ok = mbar_wait(&sh.tfull[buf], (tcount >> 1) & 1, abort, L.err);
+            const long long ql = k * gpu + gpu - 1;          // the unit's last commit group
+            bool ok = mbar_wait(&sh.gbar[ql % TC_NGBAR], (uint32_t)((ql / TC_NGBAR) & 1), abort, L.err);
             ok = __all_sync(0xffffffffu, ok);
             if (!ok) continue;                               // the next loop top stops every warp
             tc_fence_after();
-            const int J = 2 * cur.Jp + ch;                     // 128-row block of this thread's columns
+            const int J = 2 * cur.Jp + ch;                   // 128-row block of this thread's columns
             const bool skip = (job.gram_rows > 0) ? (J * TC_TILE >= job.gram_rows) : (J < cur.I);
             if (skip) {                                      // past the Gram rows, or a lower-triangle block
-                tc_fence_before();
-                mbar_arrive(&sh.tempty[buf]);
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&sh.tempty[buf]);
                 continue;
             }
-            const uint32_t taddr = tbase + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * TC_N + ch * TC_TILE);
+            const uint32_t taddr = tbase + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(buf * TC_N + ch * TC_TILE);
             const bool diag = (J == cur.I);
             const float *hcs = sh.hc[buf] + ch * TC_TILE;
             SecState *st = (job.gram_rows == 0) ? &L.st[cur.sec] : nullptr;
@@ -436,7 +498,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_screen_tc(LevelDev L, const _
                 asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
                 if (h == 1) {
                     tc_fence_before();
-                    mbar_arrive(&sh.tempty[buf]);
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&sh.tempty[buf]);
                 }
                 if (job.gram_rows > 0) {
                     float *o = job.gram_out + ((int64_t)cur.I * TC_TILE + row) * job.gram_rows + (int64_t)J * TC_TILE + h * 64;
@@ -483,7 +546,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_screen_tc(LevelDev L, const _
 
     tc_fence_before();
     __syncthreads();
-    if (warp == 1) {
+    if (warp == TC_MMA_WARP) {
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(TC_TMEM_COLS) : "memory");
     }
