@@ -165,6 +165,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", type=int, default=4)
     ap.add_argument("--precision", type=int, default=None)
+    ap.add_argument("--incremental", type=int, default=None, choices=[0, 1],
+                    help="1: incremental spectral minima (same results, row updates instead of the all-pairs screen)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--rows", type=int, default=None, help="scaled-down image (profiling); not a bench line")
@@ -191,6 +193,8 @@ def main():
         params["rnb_levels"] = args.levels
     if args.precision is not None:
         params["precision"] = args.precision
+    if args.incremental is not None:
+        params["incremental"] = args.incremental
     params["profile"] = 1
     stream = torch.cuda.current_stream()
     img_d = torch.from_numpy(img.view(np.int16)).cuda().view(torch.uint16)

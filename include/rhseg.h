@@ -80,6 +80,11 @@ typedef struct rhseg_params {
                               2 = BF16 region means on tcgen05 tensor cores, FP32 accumulate,
                               3 = FP32 on CUDA cores (the thesis kernel's arithmetic, Fig. 4.8) */
     int32_t profile;       /* 1: time every step kernel with CUDA events (stats *_ms) */
+    int32_t incremental;   /* 1: keep every region's exact best non-adjacent partner and
+                              recompute only the rows a merge touches, instead of screening
+                              all pairs each iteration (results identical; needs the
+                              binary32 rows, precision 3, else RHSEG_EINVAL).  The level-start pass and the row
+                              updates are timed as the screen (stats screen_ms). */
 } rhseg_params;
 
 /* One merge-log record.  kind 0 = adjacent merge, 1 = spectral merge,

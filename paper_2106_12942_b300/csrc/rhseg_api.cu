@@ -27,6 +27,7 @@
 #include "rhseg_kernels.cuh"
 #include "rhseg_screen_simt.cuh"
 #include "rhseg_screen_tc.cuh"
+#include "rhseg_incremental.cuh"
 
 using namespace rhseg;
 
@@ -145,6 +146,12 @@ struct rhseg_handle {
     DBuf<float> Af, kf, H;
     DBuf<double> Ad, kd;
     size_t npos = 0;
+    // incremental spectral minima
+    DBuf<uint64_t> sbK;
+    DBuf<int32_t> sbP, srow;
+    DBuf<unsigned long long> stie, sinit, ckey;
+    DBuf<uint8_t> inR;
+    DBuf<float> sT, sE, sk, sbuf;
     // per level, sized at run time
     DBuf<uint32_t> adj;
     DBuf<int64_t> aoff;
@@ -184,6 +191,8 @@ static int check_params(const rhseg_params *p, int32_t rows, int32_t cols, int32
     if (p->conv_nregions < 1 || (p->connectivity != 4 && p->connectivity != 8)) return RHSEG_EINVAL;
     if (p->min_nregions < 0 || p->n_out_levels < 0) return RHSEG_EINVAL;
     if (p->precision < 0 || p->precision > 3 || p->profile < 0 || p->profile > 1) return RHSEG_EINVAL;
+    if (p->incremental < 0 || p->incremental > 1) return RHSEG_EINVAL;
+    if (p->incremental && p->precision != 3) return RHSEG_EINVAL;   // binary32 rows only
     return RHSEG_OK;
 }
 
@@ -352,6 +361,10 @@ static ScreenConst screen_const(const rhseg_handle *h)
     c.E0 = f32_up(lam * c.eta * c.eta * (double)h->B);
     c.kscale_f = f32_up(c.kscale * (1.0 + 0x1p-30));
     c.xscale_f = (float)sc;
+    c.u_f = f32_up(c.u * (1.0 + 0x1p-30));
+    c.etaB_f = f32_up(c.eta * std::sqrt((double)h->B) * (1.0 + 0x1p-30));
+    c.onepg_f = f32_up(1.0 + 2.0 * Bp * 0x1p-24);
+    c.k1_f = (float)(sc * sc);
     return c;
 }
 
@@ -404,8 +417,21 @@ static int common_create(rhseg_handle *h, const rhseg_params *p, void *stream)
         if ((rc = h->Af.alloc(h->npos))) return rc;
         if ((rc = h->kf.alloc(h->npos))) return rc;
     }
-    if (p->precision == 1 || p->precision == 2)
+    if ((p->precision == 1 || p->precision == 2) && !p->incremental)
         if ((rc = h->H.alloc(h->npos))) return rc;
+    if (p->incremental) {
+        if ((rc = h->sbK.alloc(P))) return rc;
+        if ((rc = h->sbP.alloc(P))) return rc;
+        if ((rc = h->srow.alloc(P))) return rc;
+        if ((rc = h->stie.alloc(P))) return rc;
+        if ((rc = h->inR.alloc(P))) return rc;
+        if ((rc = h->sinit.alloc(h->npos))) return rc;
+        if ((rc = h->sT.alloc(h->npos))) return rc;
+        if ((rc = h->sE.alloc(h->npos))) return rc;
+        if ((rc = h->sk.alloc(h->npos))) return rc;
+        if ((rc = h->sbuf.alloc(h->npos * INC_RC))) return rc;
+        CK(cudaMemset(h->inR.p, 0, P));
+    }
     if (screen_uses_tcgen05(p->precision)) {
         int mr = make_operand_map(&h->tmap, h->X.p, (int64_t)h->npos, h->Bpad, p->precision);
         if (mr) {
@@ -617,6 +643,39 @@ static void launch_screen(rhseg_handle *h, const LevelDev &L)
     }
 }
 
+// Level start of the incremental mode: tiled pass `pass` over every
+// running section (operand type by precision).
+static void launch_sinit(rhseg_handle *h, const LevelDev &D, int pass)
+{
+    h->nlaunch++;
+    const int grid = h->n_sm * 4;
+    switch (h->p.precision) {
+    case 1: if (pass) k_sinit_tile<__half, 1><<<grid, 256, 0, h->stream>>>(D); else k_sinit_tile<__half, 0><<<grid, 256, 0, h->stream>>>(D); break;
+    case 2: if (pass) k_sinit_tile<__nv_bfloat16, 1><<<grid, 256, 0, h->stream>>>(D); else k_sinit_tile<__nv_bfloat16, 0><<<grid, 256, 0, h->stream>>>(D); break;
+    default: if (pass) k_sinit_tile<float, 1><<<grid, 256, 0, h->stream>>>(D); else k_sinit_tile<float, 0><<<grid, 256, 0, h->stream>>>(D); break;
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) h->launch_err = e;
+}
+
+// Per-iteration row updates of the incremental mode (binary32 rows).
+static void launch_srow_update(rhseg_handle *h, const LevelDev &D)
+{
+    h->nlaunch++;
+    const int dyn = inc_dyn_smem(h->Bpad);
+    static bool attr = false;
+    cudaError_t e = cudaSuccess;
+    if (!attr) {
+        e = cudaFuncSetAttribute(k_srow_update, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
+        attr = true;
+    }
+    if (e == cudaSuccess) {
+        k_srow_update<<<D.nsec, STEP_THREADS, dyn, h->stream>>>(D);
+        e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) h->launch_err = e;
+}
+
 static int run_impl(rhseg_handle *h)
 {
     cudaStream_t s = h->stream;
@@ -717,6 +776,9 @@ static int run_impl(rhseg_handle *h)
                                              std::max<int64_t>(1 << 16, (1ll << 24) / G.nsec));
         if (h->p.spclust_wght > 0.0)
             if ((rc = h->cand.alloc((size_t)G.nsec * cand_cap * 2))) return rc;
+        const bool inc = h->p.incremental && h->p.spclust_wght > 0.0;
+        if (inc)
+            if ((rc = h->ckey.alloc((size_t)G.nsec * cand_cap))) return rc;
         CK(cudaMemcpyAsync(h->aoff.p, aoff.data(), 8 * (G.nsec + 1), cudaMemcpyHostToDevice, s));
         CK(cudaMemcpyAsync(h->Wrow.p, W.data(), 4 * G.nsec, cudaMemcpyHostToDevice, s));
         CK(cudaMemsetAsync(h->adj.p, 0, (size_t)atot * 4, s));
@@ -741,6 +803,13 @@ static int run_impl(rhseg_handle *h)
         D.H = (h->p.precision == 1 || h->p.precision == 2) ? h->H.p : nullptr;
         D.adj = h->adj.p; D.cand = h->cand.p; D.cand_cap = cand_cap;
         D.log = h->log.p; D.err = h->err.p;
+        if (inc) {
+            D.H = nullptr;
+            D.incremental = 1;
+            D.sbK = h->sbK.p; D.sbP = h->sbP.p; D.stie = h->stie.p; D.inR = h->inR.p; D.srow = h->srow.p;
+            D.sinit = h->sinit.p; D.sT = h->sT.p; D.ckey = h->ckey.p;
+            D.sE = h->sE.p; D.sk = h->sk.p; D.inc_onepg = sc.onepg_f; D.sbuf = h->sbuf.p;
+        }
         k_init_best<<<dim3(std::max(1, std::min(64, ceil_div(m0max, 8))), G.nsec), 256, 0, s>>>(D); h->nlaunch++;
         int32_t target = (lev == 1) ? h->p.conv_nregions : h->min_nr;
         k_init_section<<<G.nsec, STEP_THREADS, 0, s>>>(D, sc, target); h->nlaunch++;
@@ -748,6 +817,25 @@ static int run_impl(rhseg_handle *h)
             k_write_rows<<<dim3(16, G.nsec), 256, 0, s>>>(D, sc); h->nlaunch++;
         }
         CK(cudaGetLastError());
+        if (inc) {
+            // every row's exact best non-adjacent partner
+            CK(cudaMemsetAsync(h->sinit.p, 0xff, h->npos * 8, s));
+            if (h->p.profile) CK(cudaEventRecord(h->prof_ev[0], s));
+            launch_sinit(h, D, 0);
+            k_sinit_exact<<<dim3(std::max(1, std::min(64, ceil_div(m0max, 8))), G.nsec), 256, 0, s>>>(D); h->nlaunch++;
+            launch_sinit(h, D, 1);
+            k_sinit_final<<<G.nsec, STEP_THREADS, 0, s>>>(D); h->nlaunch++;
+            CK(cudaGetLastError());
+            CK(h->launch_err);
+            if (h->p.profile) {
+                CK(cudaEventRecord(h->prof_ev[1], s));
+                CK(cudaEventSynchronize(h->prof_ev[1]));
+                float a = 0;
+                CK(cudaEventElapsedTime(&a, h->prof_ev[0], h->prof_ev[1]));
+                h->stats.screen_ms += a;
+                h->stats.level_screen_ms[lev - 1] += a;
+            }
+        }
         if (lev == 1) {
             h->root_m0 = sth[0].m0;
             if ((rc = h->S0.alloc((size_t)std::max(1, h->root_m0) * h->Bs))) return rc;
@@ -766,9 +854,12 @@ static int run_impl(rhseg_handle *h)
                 if (prof) CK(cudaEventRecord(h->prof_ev[(0 * chunk + k) * 2 + 1], s));
                 if (h->p.spclust_wght > 0.0) {
                     if (prof) CK(cudaEventRecord(h->prof_ev[(1 * chunk + k) * 2], s));
-                    launch_screen(h, D);
+                    if (inc) launch_srow_update(h, D);
+                    else launch_screen(h, D);
                     if (prof) CK(cudaEventRecord(h->prof_ev[(1 * chunk + k) * 2 + 1], s));
-                    k_spec_step<<<G.nsec, STEP_THREADS, 0, s>>>(D, sc); h->nlaunch++;
+                    if (inc) k_spec_inc<<<G.nsec, STEP_THREADS, 0, s>>>(D, sc);
+                    else k_spec_step<<<G.nsec, STEP_THREADS, 0, s>>>(D, sc);
+                    h->nlaunch++;
                     k_write_rows<<<dim3(16, G.nsec), 256, 0, s>>>(D, sc); h->nlaunch++;
                     if (prof) CK(cudaEventRecord(h->prof_ev[(2 * chunk + k) * 2 + 1], s));
                 }
@@ -1110,6 +1201,8 @@ extern "C" void rhseg_destroy(rhseg_handle *h)
     h->srcslot.release(); h->slot_of_id.release(); h->seam_list.release(); h->nseam.release();
     h->split_key.release();
     h->slots[0].release(); h->slots[1].release();
+    h->sbK.release(); h->sbP.release(); h->srow.release(); h->stie.release(); h->sinit.release();
+    h->ckey.release(); h->inR.release(); h->sT.release(); h->sE.release(); h->sk.release(); h->sbuf.release();
     h->slot_of_pos.release(); h->X.release(); h->Af.release(); h->kf.release(); h->H.release(); h->Ad.release(); h->kd.release();
     h->adj.release(); h->aoff.release(); h->Wrow.release(); h->ref.release(); h->cand.release(); h->st.release();
     h->log.release(); h->err.release(); h->active.release();

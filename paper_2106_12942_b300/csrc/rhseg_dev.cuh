@@ -36,6 +36,8 @@ struct SecState {
     int32_t madj, mspec;   // merges by kind
     int32_t nsplit;        // seam splits applied at the start of this level
     int32_t rows_from;     // > 0: the position list was rebuilt this iteration (old extent)
+    int32_t pm_a[2], pm_b[2];   // incremental mode: merges (survivor, absorbed) whose rows are pending
+    int32_t npm;
 };
 
 // Geometry and buffers of the level in flight (device pointers).  Arrays
@@ -79,6 +81,19 @@ struct LevelDev {
     // log
     void *log;                 // rhseg_merge records
     int32_t *err;              // device error word
+    // incremental spectral minima (null unless that mode is on)
+    int32_t incremental;
+    uint64_t *sbK;             // per slot: K bits of the best non-adjacent pair
+    int32_t *sbP;              // per slot: partner slot of that pair
+    unsigned long long *stie;  // per slot: scratch (lowest slot pair among equal keys)
+    uint8_t *inR;              // per slot: scratch (row listed for recomputation)
+    int32_t *srow;             // per slot: scratch (rows to recompute)
+    unsigned long long *sinit; // per position: approximate argmin, then the row's bound
+    float *sT;                 // per position: the row's binary32 threshold
+    float *sE, *sk;            // per position: operand error norm, 4^-sigma / n (both rounded up)
+    float inc_onepg;           // 1 + gamma_B for a binary32 sum of Bpad non-negative terms (rounded up)
+    float *sbuf;               // per position x 8: scratch (sums of squared differences of a row update)
+    unsigned long long *ckey;  // [nsec][cand_cap] exact keys of candidates
 };
 
 // ---------------------------------------------------------------------------

@@ -249,6 +249,9 @@ struct ScreenConst {
     //   Fq = 1 - gamma - 4 (1 + 1/delta) u^2 and E0 = 4 (1 + 1/delta) eta^2 B,
     //   from eps^2 <= 2 u^2 q + 2 eta^2 B
     float Fq, E0, kscale_f, xscale_f;
+    // incremental minima (binary32 rows): eps = u_f * sqrt(q * onepg_f) + etaB_f
+    // bounds ||x^ - x|| (rounded up); k1_f / n = 4^-sigma / n (rounded up)
+    float u_f, etaB_f, onepg_f, k1_f;
 };
 
 template <typename T>
@@ -336,6 +339,12 @@ __device__ void warp_write_row(const LevelDev &L, int sec, int slot, int pos, co
     if (lane == 0) {
         L.Af[L.poff[sec] + pos] = __fmaf_rd(q, sc.Fq, -sc.E0);
         L.kf[L.poff[sec] + pos] = __fdiv_ru(sc.kscale_f, __int2float_rd((int)n));
+        if (L.sE != nullptr) {
+            // operand error norm and 4^-sigma/n for the incremental minima's key bound
+            const float e = __fadd_ru(__fmul_ru(sc.u_f, __fsqrt_ru(__fmul_ru(q, sc.onepg_f))), sc.etaB_f);
+            L.sE[L.poff[sec] + pos] = __fmul_ru(e, 1.0f + 0x1p-20f);
+            L.sk[L.poff[sec] + pos] = __fdiv_ru(sc.k1_f, __int2float_rd((int)n));
+        }
     }
 }
 
@@ -395,6 +404,8 @@ __global__ void __launch_bounds__(STEP_THREADS) k_init_section(LevelDev L, Scree
         st->nadj = pc / 2;
         st->mc = m0;
         st->rows_from = m0;
+        st->npm = 0;
+        st->ncand = 0;
         st->done = (m0 <= target) ? 1 : 0;
         st->Kadj = __longlong_as_double(0x7FF0000000000000ll);
         st->tthr = st->Kadj;
@@ -610,6 +621,7 @@ __device__ void block_merge(const LevelDev &L, int sec, SecState &st, int a, int
         L.absorbed_at[ro + b] = ord;
         L.bestK[ro + b] = RHSEG_KEY_NONE;
         L.bestP[ro + b] = -1;
+        if (L.sbK) { L.sbK[ro + b] = RHSEG_KEY_NONE; L.sbP[ro + b] = -1; }
         st.count -= 1;
         rhseg_merge m;
         m.level = L.level; m.section = sec; m.step = st.iter; m.kind = kind;
@@ -819,6 +831,11 @@ __global__ void __launch_bounds__(STEP_THREADS, 2) k_adj_step(LevelDev L, Screen
         Kadj = __longlong_as_double((long long)best.k);
         block_merge(L, sec, st, (int)best.lo, (int)best.hi, Kadj, 0, sc, sm);
         merged = 1;
+        if (L.incremental && threadIdx.x == 0) {      // rows to recompute for the spectral minima
+            st.pm_a[st.npm] = (int)best.lo;
+            st.pm_b[st.npm] = (int)best.hi;
+            st.npm += 1;
+        }
     }
     __syncthreads();
     if (threadIdx.x == 0) {

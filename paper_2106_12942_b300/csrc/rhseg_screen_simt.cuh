@@ -30,7 +30,8 @@ __host__ __device__ __forceinline__ long long tc_section_units(long long mc)
 
 // Exclusive prefix over sections of the number of upper-triangle tiles of
 // each pending section (tile edge `tile`; tile == 0 counts the tensor-core
-// screen's units instead).  Whole block; result in pre[0..nsec].
+// screen's units instead; tile < 0 counts tiles of edge -tile of every
+// section still running).  Whole block; result in pre[0..nsec].
 __device__ void block_tile_prefix(const LevelDev &L, int tile, long long *pre)
 {
     int nsec = L.nsec;
@@ -44,7 +45,12 @@ __device__ void block_tile_prefix(const LevelDev &L, int tile, long long *pre)
         long long t = 0;
         if (k < per && s < nsec) {
             const SecState &st = L.st[s];
-            if (st.spec_pending && st.tthr < __longlong_as_double(0x7FF0000000000000ll)) {
+            if (tile < 0) {
+                if (!st.done) {
+                    long long nb = (st.mc + (-tile) - 1) / (-tile);
+                    t = nb * (nb + 1) / 2;
+                }
+            } else if (st.spec_pending && st.tthr < __longlong_as_double(0x7FF0000000000000ll)) {
                 if (tile == 0) {
                     t = tc_section_units(st.mc);
                 } else {
