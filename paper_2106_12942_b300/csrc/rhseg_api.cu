@@ -151,7 +151,8 @@ struct rhseg_handle {
     DBuf<int32_t> sbP, srow;
     DBuf<unsigned long long> stie, sinit, ckey;
     DBuf<uint8_t> inR;
-    DBuf<float> sT, sE, sk, sbuf;
+    DBuf<float> sT, sE, sk, sbuf, srowx;
+    DBuf<IncInfo> sinfo;
     // per level, sized at run time
     DBuf<uint32_t> adj;
     DBuf<int64_t> aoff;
@@ -429,7 +430,9 @@ static int common_create(rhseg_handle *h, const rhseg_params *p, void *stream)
         if ((rc = h->sT.alloc(h->npos))) return rc;
         if ((rc = h->sE.alloc(h->npos))) return rc;
         if ((rc = h->sk.alloc(h->npos))) return rc;
-        if ((rc = h->sbuf.alloc(h->npos * INC_RC))) return rc;
+        if ((rc = h->sbuf.alloc(h->npos * INC_RCAP))) return rc;
+        if ((rc = h->srowx.alloc((size_t)h->geo[p->rnb_levels].nsec * h->Bpad * INC_RCAP))) return rc;
+        if ((rc = h->sinfo.alloc((size_t)h->geo[p->rnb_levels].nsec))) return rc;
         CK(cudaMemset(h->inR.p, 0, P));
     }
     if (screen_uses_tcgen05(p->precision)) {
@@ -658,19 +661,24 @@ static void launch_sinit(rhseg_handle *h, const LevelDev &D, int pass)
     if (e != cudaSuccess) h->launch_err = e;
 }
 
-// Per-iteration row updates of the incremental mode (binary32 rows).
+// Per-iteration row updates of the incremental mode (binary32 rows): the
+// rows to recompute, the sums pass over many blocks per section, then the
+// exact minima and pushes.
 static void launch_srow_update(rhseg_handle *h, const LevelDev &D)
 {
-    h->nlaunch++;
     const int dyn = inc_dyn_smem(h->Bpad);
     static bool attr = false;
     cudaError_t e = cudaSuccess;
     if (!attr) {
-        e = cudaFuncSetAttribute(k_srow_update, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
+        e = cudaFuncSetAttribute(k_srow_sums, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_srow_finish, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
         attr = true;
     }
     if (e == cudaSuccess) {
-        k_srow_update<<<D.nsec, STEP_THREADS, dyn, h->stream>>>(D);
+        k_srow_begin<<<D.nsec, STEP_THREADS, 0, h->stream>>>(D);
+        k_srow_sums<<<dim3(INC_SUM_BLOCKS, D.nsec), STEP_THREADS, dyn, h->stream>>>(D);
+        k_srow_finish<<<D.nsec, STEP_THREADS, dyn, h->stream>>>(D);
+        h->nlaunch += 3;
         e = cudaGetLastError();
     }
     if (e != cudaSuccess) h->launch_err = e;
@@ -809,6 +817,7 @@ static int run_impl(rhseg_handle *h)
             D.sbK = h->sbK.p; D.sbP = h->sbP.p; D.stie = h->stie.p; D.inR = h->inR.p; D.srow = h->srow.p;
             D.sinit = h->sinit.p; D.sT = h->sT.p; D.ckey = h->ckey.p;
             D.sE = h->sE.p; D.sk = h->sk.p; D.inc_onepg = sc.onepg_f; D.sbuf = h->sbuf.p;
+            D.srowx = h->srowx.p; D.sinfo = h->sinfo.p;
         }
         k_init_best<<<dim3(std::max(1, std::min(64, ceil_div(m0max, 8))), G.nsec), 256, 0, s>>>(D); h->nlaunch++;
         int32_t target = (lev == 1) ? h->p.conv_nregions : h->min_nr;
@@ -1203,6 +1212,7 @@ extern "C" void rhseg_destroy(rhseg_handle *h)
     h->slots[0].release(); h->slots[1].release();
     h->sbK.release(); h->sbP.release(); h->srow.release(); h->stie.release(); h->sinit.release();
     h->ckey.release(); h->inR.release(); h->sT.release(); h->sE.release(); h->sk.release(); h->sbuf.release();
+    h->srowx.release(); h->sinfo.release();
     h->slot_of_pos.release(); h->X.release(); h->Af.release(); h->kf.release(); h->H.release(); h->Ad.release(); h->kd.release();
     h->adj.release(); h->aoff.release(); h->Wrow.release(); h->ref.release(); h->cand.release(); h->st.release();
     h->log.release(); h->err.release(); h->active.release();

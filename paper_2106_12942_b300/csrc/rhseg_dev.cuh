@@ -93,6 +93,8 @@ struct LevelDev {
     float *sE, *sk;            // per position: operand error norm, 4^-sigma / n (both rounded up)
     float inc_onepg;           // 1 + gamma_B for a binary32 sum of Bpad non-negative terms (rounded up)
     float *sbuf;               // per position x 8: scratch (sums of squared differences of a row update)
+    float *srowx;              // per section: staged row vectors of a row update [Bpad][8]
+    struct IncInfo *sinfo;     // per section: state of a row update between its kernels
     unsigned long long *ckey;  // [nsec][cand_cap] exact keys of candidates
 };
 

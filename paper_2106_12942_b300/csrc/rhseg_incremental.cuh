@@ -33,6 +33,7 @@ namespace rhseg {
 constexpr int INC_TILE = 64;
 constexpr int INC_KC = 16;
 constexpr int INC_RC = 8;               // rows evaluated per pass over a section's operand rows
+constexpr int INC_RCAP = 32;            // rows of one update evaluated by the many-block sums pass
 
 __device__ __forceinline__ unsigned long long inc_pack_pair(int i, int j)
 {
@@ -353,7 +354,7 @@ __global__ void __launch_bounds__(STEP_THREADS) k_sinit_final(LevelDev L)
 // loads), stored per position in sbuf, and each row's approximate argmin.
 template <int RC>
 __device__ void inc_pass_sums(const LevelDev &L, int sec, const int32_t *rows, int nr, const float *xs,
-                              const float *rAk, unsigned long long *apx)
+                              const float *rAk, unsigned long long *apx, int p_lo, int p_hi, int sb_off)
 {
     const int64_t ro = L.roff[sec], pb = L.poff[sec];
     const int W = L.W[sec];
@@ -363,7 +364,8 @@ __device__ void inc_pass_sums(const LevelDev &L, int sec, const int32_t *rows, i
     unsigned long long lbest[RC];
 #pragma unroll
     for (int r = 0; r < RC; r++) lbest[r] = ~0ull;
-    for (int p = threadIdx.x; p < mc; p += blockDim.x) {
+    (void)mc;
+    for (int p = p_lo + (int)threadIdx.x; p < p_hi; p += blockDim.x) {
         const int j = L.slot_of_pos[pb + p];
         if (!L.alive[ro + j]) continue;
         const float4 *xj = (const float4 *)(X + (pb + p) * L.Bpad);
@@ -383,7 +385,7 @@ __device__ void inc_pass_sums(const LevelDev &L, int sec, const int32_t *rows, i
                 }
             }
         }
-        float *sb = L.sbuf + (pb + p) * INC_RC;
+        float *sb = L.sbuf + (pb + p) * INC_RCAP + sb_off;
 #pragma unroll
         for (int r = 0; r < RC; r++) sb[r] = g[r];
         const float kj = L.sk[pb + p];
@@ -413,7 +415,7 @@ __device__ void inc_pass_sums(const LevelDev &L, int sec, const int32_t *rows, i
 // each row's own minimum (bound <= its U) and, for the merged rows, for the
 // partners whose best they may improve (bound <= the partner's best).
 __device__ void inc_pass_test(const LevelDev &L, int sec, const int32_t *rows, int nr, int nprop, const float *rAk,
-                              const float *rT, uint32_t *ncand_s)
+                              const float *rT, uint32_t *ncand_s, int sb_off)
 {
     const int64_t ro = L.roff[sec], pb = L.poff[sec];
     const int W = L.W[sec];
@@ -423,7 +425,7 @@ __device__ void inc_pass_test(const LevelDev &L, int sec, const int32_t *rows, i
     for (int p = threadIdx.x; p < mc; p += blockDim.x) {
         const int j = L.slot_of_pos[pb + p];
         if (!L.alive[ro + j]) continue;
-        const float *sb = L.sbuf + (pb + p) * INC_RC;
+        const float *sb = L.sbuf + (pb + p) * INC_RCAP + sb_off;
         const float Ej = L.sE[pb + p], kj = L.sk[pb + p];
         float Tj = 0.0f;
         bool inr = false;
@@ -448,47 +450,164 @@ __device__ void inc_pass_test(const LevelDev &L, int sec, const int32_t *rows, i
     }
 }
 
-__device__ void inc_pass_sums_any(const LevelDev &L, int sec, const int32_t *rows, int nr, const float *xs,
-                                  const float *rAk, unsigned long long *apx)
-{
-    switch (nr) {
-    case 1: inc_pass_sums<1>(L, sec, rows, nr, xs, rAk, apx); break;
-    case 2: inc_pass_sums<2>(L, sec, rows, nr, xs, rAk, apx); break;
-    case 3: inc_pass_sums<3>(L, sec, rows, nr, xs, rAk, apx); break;
-    case 4: inc_pass_sums<4>(L, sec, rows, nr, xs, rAk, apx); break;
-    case 5: case 6: inc_pass_sums<6>(L, sec, rows, nr, xs, rAk, apx); break;
-    default: inc_pass_sums<8>(L, sec, rows, nr, xs, rAk, apx); break;
-    }
-}
 
-// Shared memory of the update kernel beyond StepSmem: staged row vectors
-// [Bpad][INC_RC] (binary32).
+// Shared memory of the update kernels: staged row vectors [Bpad][INC_RC]
+// (binary32).
 __host__ __device__ constexpr int inc_dyn_smem(int Bpad) { return Bpad * INC_RC * 4; }
 
-__global__ void __launch_bounds__(STEP_THREADS) k_srow_update(LevelDev L)
+constexpr int INC_SUM_BLOCKS = 8;      // blocks per section of the sums pass
+
+// Per-section state of one row update, between its three kernels.
+struct IncInfo {
+    int32_t nrows, nmerged, nstaged;          // rows to recompute; merged survivors; rows staged (<= INC_RCAP)
+    int32_t active;
+    int32_t crow[INC_RCAP];
+    float rAk[2 * INC_RCAP];
+    unsigned long long apx[INC_RCAP];
+};
+
+// Exact bound, pass B, exact keys, minima and pushes of a chunk whose sums
+// are in sbuf and approximate argmins in apx_in (whole block).
+__device__ long long inc_chunk_finish(const LevelDev &L, int sec, StepSmem &sm, int m0, const int32_t *crow_s,
+                                      int nr, int nprop, const float *rAk_s, const unsigned long long *apx_s,
+                                      float *rT, unsigned long long *rK, unsigned long long *rTie,
+                                      unsigned long long *rU, uint32_t *ncand_s, int64_t &fallbacks, int sb_off)
+{
+    const int64_t ro = L.roff[sec];
+    // exact key of each row's approximate best: the bound U
+    {
+        const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        if (wid < nr) {
+            const int r = crow_s[wid];
+            const unsigned long long a = apx_s[wid];
+            uint64_t U = RHSEG_KEY_NONE;
+            int j = -1;
+            if (a != ~0ull) {
+                j = (int)(uint32_t)a;
+                U = dbits(warp_key(L.S + (ro + r) * L.Bs, L.n[ro + r], L.S + (ro + j) * L.Bs, L.n[ro + j], L.B, L.err));
+            }
+            if (lane == 0) {
+                rU[wid] = U;
+                rK[wid] = U;
+                rTie[wid] = (j >= 0) ? inc_pack_pair(r, j) : ~0ull;
+                rT[wid] = (j >= 0) ? inc_thr_le(U) : __int_as_float(0x7fc00000);
+            }
+        }
+        if (threadIdx.x == 0) *ncand_s = 0;
+    }
+    __syncthreads();
+    // pass B: candidates for each row's own minimum, and the merged rows'
+    // keys that may improve another row's best
+    inc_pass_test(L, sec, crow_s, nr, nprop, rAk_s, rT, ncand_s, sb_off);
+    __syncthreads();
+    const uint32_t nc = *ncand_s;
+    if ((int64_t)nc > L.cand_cap) {
+        // overflow: exact scans (merged rows push to every row, one row at a time)
+        const int wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+        for (int r = wid; r < nr; r += nw) warp_spectral_row_exact(L, sec, crow_s[r], m0);
+        __syncthreads();
+        for (int r = 0; r < nprop; r++) {
+            const int a = crow_s[r];
+            const uint32_t *rowA = L.adj + L.aoff[sec] + (int64_t)a * L.W[sec];
+            for (int j = wid; j < m0; j += nw) {
+                if (j == a || !L.alive[ro + j] || L.inR[ro + j]) continue;
+                if ((rowA[j >> 5] >> (j & 31)) & 1) continue;
+                const double K = warp_key(L.S + (ro + a) * L.Bs, L.n[ro + a], L.S + (ro + j) * L.Bs, L.n[ro + j], L.B, L.err);
+                if ((threadIdx.x & 31) == 0) {
+                    const PairKey old = pk_make(L.sbK[ro + j], j, L.sbP[ro + j] < 0 ? j : L.sbP[ro + j]);
+                    const PairKey nc2 = pk_make(dbits(K), j, a);
+                    if (L.sbK[ro + j] == RHSEG_KEY_NONE || pk_less(nc2, old)) { L.sbK[ro + j] = nc2.k; L.sbP[ro + j] = a; }
+                }
+            }
+            __syncthreads();
+        }
+        fallbacks += 1;
+        __syncthreads();
+        return 0;
+    }
+    // exact keys of the candidates (row index r in the low bits -> slot)
+    const uint32_t *cand = L.cand + (int64_t)sec * L.cand_cap * 2;
+    unsigned long long *ck = L.ckey + (int64_t)sec * L.cand_cap;
+    for (uint32_t q0 = 0; q0 < nc; q0 += PAIR_CAP) {
+        const uint32_t cnt = min((uint32_t)PAIR_CAP, nc - q0);
+        __syncthreads();
+        for (uint32_t c = threadIdx.x; c < cnt; c += blockDim.x) {
+            sm.pi[c] = crow_s[cand[2 * (q0 + c)] & 0xffu];
+            sm.pj[c] = (int32_t)cand[2 * (q0 + c) + 1];
+        }
+        __syncthreads();
+        block_keys(L, ro, sm.pi, sm.pj, sm.pkey, (int)cnt);
+        __syncthreads();
+        for (uint32_t c = threadIdx.x; c < cnt; c += blockDim.x) ck[q0 + c] = sm.pkey[c];
+    }
+    __syncthreads();
+    // own minima: key, then slot pair
+    for (uint32_t c = threadIdx.x; c < nc; c += blockDim.x)
+        if (cand[2 * c] & 0x40000000u) atomicMin(&rK[cand[2 * c] & 0xffu], ck[c]);
+    __syncthreads();
+    if (threadIdx.x < nr && rK[threadIdx.x] != rU[threadIdx.x]) rTie[threadIdx.x] = ~0ull;
+    __syncthreads();
+    for (uint32_t c = threadIdx.x; c < nc; c += blockDim.x) {
+        const uint32_t w0 = cand[2 * c];
+        const int r = (int)(w0 & 0xffu);
+        if ((w0 & 0x40000000u) && ck[c] == rK[r]) atomicMin(&rTie[r], inc_pack_pair(crow_s[r], (int)cand[2 * c + 1]));
+    }
+    __syncthreads();
+    if (threadIdx.x < nr) {
+        const int r = threadIdx.x, s2 = crow_s[r];
+        const unsigned long long p = rTie[r];
+        L.sbK[ro + s2] = rK[r];
+        if (rK[r] == RHSEG_KEY_NONE || p == ~0ull) {
+            L.sbP[ro + s2] = -1;
+        } else {
+            const uint32_t lo = (uint32_t)(p >> 32), hi = (uint32_t)p;
+            L.sbP[ro + s2] = (int32_t)(lo == (uint32_t)s2 ? hi : lo);
+        }
+    }
+    __syncthreads();
+    // pushes of the merged rows' keys, one merged row at a time (each
+    // partner appears once per merged row)
+    for (int r = 0; r < nprop; r++) {
+        const int a = crow_s[r];
+        for (uint32_t c = threadIdx.x; c < nc; c += blockDim.x) {
+            const uint32_t w0 = cand[2 * c];
+            if ((int)(w0 & 0xffu) != r || !(w0 & 0x80000000u)) continue;
+            const int j = (int)cand[2 * c + 1];
+            const uint64_t K = ck[c];
+            const uint64_t oldK = L.sbK[ro + j];
+            const int op = L.sbP[ro + j];
+            const bool better = (oldK == RHSEG_KEY_NONE) ||
+                                pk_less(pk_make(K, j, a), pk_make(oldK, j, op < 0 ? j : op));
+            if (better) { L.sbK[ro + j] = K; L.sbP[ro + j] = a; }
+        }
+        __syncthreads();
+    }
+    return (long long)nc;
+}
+
+// Row update, step 1 (one block per section): the rows to recompute
+// (merged survivors first, then the rows whose best was a merged slot) and
+// the first chunk's row terms; the pending merges are consumed.
+__global__ void __launch_bounds__(STEP_THREADS) k_srow_begin(LevelDev L)
 {
     const int sec = blockIdx.x;
     if (sec >= L.nsec) return;
-    __shared__ StepSmem sm;
-    __shared__ int32_t crow[INC_RC];
-    __shared__ float rAk[2 * INC_RC], rT[INC_RC];
-    __shared__ unsigned long long apx[INC_RC], rK[INC_RC], rTie[INC_RC], rU[INC_RC];
-    __shared__ uint32_t ncand_s;
     __shared__ int32_t nR, nM;
-    extern __shared__ float xs[];                  // [Bpad][INC_RC]
+    __shared__ SecState st;
+    IncInfo *info = L.sinfo + sec;
     SecState *stg = &L.st[sec];
-    if (threadIdx.x == 0) sm.st = *stg;
+    if (threadIdx.x == 0) st = *stg;
     __syncthreads();
-    SecState &st = sm.st;
     if (st.done || st.npm == 0) {
-        if (threadIdx.x == 0 && st.npm != 0) stg->npm = 0;
+        if (threadIdx.x == 0) {
+            info->active = 0;
+            if (st.npm != 0) stg->npm = 0;
+        }
         return;
     }
     const int64_t ro = L.roff[sec], pb = L.poff[sec];
     const int m0 = st.m0;
-    int32_t *R = L.srow + ro;                      // list of rows to recompute (slots)
-    // ---- the rows: merged survivors first (they push their keys), then rows
-    //      whose best was a merged slot ----
+    int32_t *R = L.srow + ro;
     if (threadIdx.x == 0) {
         int n = 0;
         for (int k = 0; k < st.npm; k++) {
@@ -512,154 +631,155 @@ __global__ void __launch_bounds__(STEP_THREADS) k_srow_update(LevelDev L)
     }
     __syncthreads();
     const int nrows = nR, nmerged = nM;
+    const int ns = min(INC_RCAP, nrows);
+    for (int r = threadIdx.x; r < INC_RCAP; r += blockDim.x) {
+        if (r < ns) {
+            const int s = R[r];
+            const int p = L.pos_of_slot[ro + s];
+            info->crow[r] = s;
+            info->rAk[2 * r] = L.sE[pb + p];
+            info->rAk[2 * r + 1] = L.sk[pb + p];
+        } else {
+            info->crow[r] = -1;
+            info->rAk[2 * r] = 0.0f;
+            info->rAk[2 * r + 1] = 1.0f;
+        }
+        info->apx[r] = ~0ull;
+    }
+    // the staged rows' vectors, per chunk of INC_RC rows [Bpad][INC_RC]
+    float *xg = L.srowx + (int64_t)sec * L.Bpad * INC_RCAP;
+    const int nchunk = (ns + INC_RC - 1) / INC_RC;
+    for (int e = threadIdx.x; e < nchunk * L.Bpad * INC_RC; e += blockDim.x) {
+        const int c = e / (L.Bpad * INC_RC), rem = e % (L.Bpad * INC_RC);
+        const int b = rem / INC_RC, r = c * INC_RC + rem % INC_RC;
+        float v = 0.0f;
+        if (r < ns) v = ((const float *)L.X)[(pb + L.pos_of_slot[ro + R[r]]) * L.Bpad + b];
+        xg[e] = v;
+    }
+    if (threadIdx.x == 0) {
+        info->nrows = nrows;
+        info->nmerged = nmerged;
+        info->nstaged = ns;
+        info->active = nrows > 0 ? 1 : 0;
+        stg->npm = 0;
+    }
+}
+
+// Row update, step 2: pass A of the first chunk, INC_SUM_BLOCKS blocks per
+// section over slices of the positions.
+__global__ void __launch_bounds__(STEP_THREADS) k_srow_sums(LevelDev L)
+{
+    const int sec = blockIdx.y;
+    if (sec >= L.nsec) return;
+    IncInfo *info = L.sinfo + sec;
+    if (!info->active) return;
+    __shared__ int32_t crow[INC_RC];
+    __shared__ float rAk[2 * INC_RC];
+    __shared__ unsigned long long apx[INC_RC];
+    extern __shared__ float xs[];
+    const int ns = info->nstaged;
+    const int mc = L.st[sec].mc;
+    const int per = (mc + gridDim.x - 1) / gridDim.x;
+    const int lo = blockIdx.x * per, hi = min(mc, lo + per);
+    for (int c0 = 0; c0 < ns; c0 += INC_RC) {
+        const int nr = min(INC_RC, ns - c0);
+        __syncthreads();
+        if (threadIdx.x < INC_RC) {
+            crow[threadIdx.x] = info->crow[c0 + threadIdx.x];
+            rAk[2 * threadIdx.x] = info->rAk[2 * (c0 + threadIdx.x)];
+            rAk[2 * threadIdx.x + 1] = info->rAk[2 * (c0 + threadIdx.x) + 1];
+            apx[threadIdx.x] = ~0ull;
+        }
+        const float *xg = L.srowx + ((int64_t)sec * INC_RCAP + c0) * L.Bpad;
+        for (int e = threadIdx.x; e < L.Bpad * INC_RC; e += blockDim.x) xs[e] = xg[e];
+        __syncthreads();
+        switch (nr) {
+        case 1: inc_pass_sums<1>(L, sec, crow, nr, xs, rAk, apx, lo, hi, c0); break;
+        case 2: inc_pass_sums<2>(L, sec, crow, nr, xs, rAk, apx, lo, hi, c0); break;
+        case 3: inc_pass_sums<3>(L, sec, crow, nr, xs, rAk, apx, lo, hi, c0); break;
+        case 4: inc_pass_sums<4>(L, sec, crow, nr, xs, rAk, apx, lo, hi, c0); break;
+        case 5: case 6: inc_pass_sums<6>(L, sec, crow, nr, xs, rAk, apx, lo, hi, c0); break;
+        default: inc_pass_sums<8>(L, sec, crow, nr, xs, rAk, apx, lo, hi, c0); break;
+        }
+        __syncthreads();
+        if (threadIdx.x < nr && apx[threadIdx.x] != ~0ull) atomicMin(&info->apx[c0 + threadIdx.x], apx[threadIdx.x]);
+    }
+}
+
+// Row update, step 3 (one block per section): the first chunk's exact
+// minima and pushes; further chunks (rows past INC_RC) in-block.
+__global__ void __launch_bounds__(STEP_THREADS) k_srow_finish(LevelDev L)
+{
+    const int sec = blockIdx.x;
+    if (sec >= L.nsec) return;
+    __shared__ StepSmem sm;
+    __shared__ int32_t crow[INC_RC];
+    __shared__ float rAk[2 * INC_RC], rT[INC_RC];
+    __shared__ unsigned long long apx[INC_RC], rK[INC_RC], rTie[INC_RC], rU[INC_RC];
+    __shared__ uint32_t ncand_s;
+    extern __shared__ float xs[];
+    const IncInfo *info = L.sinfo + sec;
+    if (!info->active) return;
+    SecState *stg = &L.st[sec];
+    const int64_t ro = L.roff[sec], pb = L.poff[sec];
+    const int m0 = stg->m0;
+    const int32_t *R = L.srow + ro;
+    const int nrows = info->nrows, nmerged = info->nmerged;
+    int64_t fallbacks = 0;
     long long keys = 0;
     for (int c0 = 0; c0 < nrows; c0 += INC_RC) {
         const int nr = min(INC_RC, nrows - c0);
         const int nprop = max(0, min(nr, nmerged - c0));
-        // stage the rows
-        if (threadIdx.x < INC_RC) {
-            const int r = threadIdx.x;
-            if (r < nr) {
-                const int s = R[c0 + r];
-                const int p = L.pos_of_slot[ro + s];
-                crow[r] = s;
-                rAk[2 * r] = L.sE[pb + p];
-                rAk[2 * r + 1] = L.sk[pb + p];
-            } else {
-                crow[r] = -1;
+        __syncthreads();
+        int sb_off = c0;
+        if (c0 < info->nstaged) {
+            if (threadIdx.x < INC_RC) {
+                crow[threadIdx.x] = info->crow[c0 + threadIdx.x];
+                rAk[2 * threadIdx.x] = info->rAk[2 * (c0 + threadIdx.x)];
+                rAk[2 * threadIdx.x + 1] = info->rAk[2 * (c0 + threadIdx.x) + 1];
+                apx[threadIdx.x] = info->apx[c0 + threadIdx.x];
             }
-            apx[r] = ~0ull;
-        }
-        __syncthreads();
-        for (int e = threadIdx.x; e < L.Bpad * INC_RC; e += blockDim.x) {
-            const int b = e / INC_RC, r = e % INC_RC;
-            float v = 0.0f;
-            if (r < nr) v = ((const float *)L.X)[(pb + L.pos_of_slot[ro + crow[r]]) * L.Bpad + b];
-            xs[b * INC_RC + r] = v;
-        }
-        if (threadIdx.x == 0) ncand_s = 0;
-        __syncthreads();
-        // pass A: sums of squared differences and the approximate argmin per row
-        inc_pass_sums_any(L, sec, crow, nr, xs, rAk, apx);
-        __syncthreads();
-        // exact key of each row's approximate best: the bound U
-        {
-            const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-            if (wid < nr) {
-                const int r = crow[wid];
-                const unsigned long long a = apx[wid];
-                uint64_t U = RHSEG_KEY_NONE;
-                int j = -1;
-                if (a != ~0ull) {
-                    j = (int)(uint32_t)a;
-                    U = dbits(warp_key(L.S + (ro + r) * L.Bs, L.n[ro + r], L.S + (ro + j) * L.Bs, L.n[ro + j], L.B, L.err));
-                }
-                if (lane == 0) {
-                    rU[wid] = U;
-                    rK[wid] = U;
-                    rTie[wid] = (j >= 0) ? inc_pack_pair(r, j) : ~0ull;
-                    rT[wid] = (j >= 0) ? inc_thr_le(U) : __int_as_float(0x7fc00000);
-                }
-            }
-        }
-        __syncthreads();
-        // pass B: candidates for each row's own minimum, and the merged rows'
-        // keys that may improve another row's best
-        inc_pass_test(L, sec, crow, nr, nprop, rAk, rT, &ncand_s);
-        __syncthreads();
-        const uint32_t nc = ncand_s;
-        if ((int64_t)nc > L.cand_cap) {
-            // overflow: exact scans (merged rows push to every row, one row at a time)
-            const int wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-            for (int r = wid; r < nr; r += nw) warp_spectral_row_exact(L, sec, crow[r], m0);
             __syncthreads();
-            for (int r = 0; r < nprop; r++) {
-                const int a = crow[r];
-                const uint32_t *rowA = L.adj + L.aoff[sec] + (int64_t)a * L.W[sec];
-                for (int j = wid; j < m0; j += nw) {
-                    if (j == a || !L.alive[ro + j] || L.inR[ro + j]) continue;
-                    if ((rowA[j >> 5] >> (j & 31)) & 1) continue;
-                    const double K = warp_key(L.S + (ro + a) * L.Bs, L.n[ro + a], L.S + (ro + j) * L.Bs, L.n[ro + j], L.B, L.err);
-                    if ((threadIdx.x & 31) == 0) {
-                        const PairKey old = pk_make(L.sbK[ro + j], j, L.sbP[ro + j] < 0 ? j : L.sbP[ro + j]);
-                        const PairKey nc2 = pk_make(dbits(K), j, a);
-                        if (L.sbK[ro + j] == RHSEG_KEY_NONE || pk_less(nc2, old)) { L.sbK[ro + j] = nc2.k; L.sbP[ro + j] = a; }
-                    }
+        } else {
+            sb_off = 0;                            // the staged chunks are finished: reuse their scratch
+            // a further chunk: stage and pass A in this block
+            if (threadIdx.x < INC_RC) {
+                const int r = threadIdx.x;
+                if (r < nr) {
+                    const int s2 = R[c0 + r];
+                    const int p = L.pos_of_slot[ro + s2];
+                    crow[r] = s2;
+                    rAk[2 * r] = L.sE[pb + p];
+                    rAk[2 * r + 1] = L.sk[pb + p];
+                } else {
+                    crow[r] = -1;
+                    rAk[2 * r] = 0.0f;
+                    rAk[2 * r + 1] = 1.0f;
                 }
-                __syncthreads();
+                apx[r] = ~0ull;
             }
-            if (threadIdx.x == 0) st.fallbacks += 1;
             __syncthreads();
-            continue;
+            for (int e = threadIdx.x; e < L.Bpad * INC_RC; e += blockDim.x) {
+                const int b = e / INC_RC, r = e % INC_RC;
+                float v = 0.0f;
+                if (r < nr) v = ((const float *)L.X)[(pb + L.pos_of_slot[ro + crow[r]]) * L.Bpad + b];
+                xs[b * INC_RC + r] = v;
+            }
+            __syncthreads();
+            inc_pass_sums<8>(L, sec, crow, nr, xs, rAk, apx, 0, stg->mc, 0);
+            __syncthreads();
         }
+        const long long nc = inc_chunk_finish(L, sec, sm, m0, crow, nr, nprop, rAk, apx, rT, rK, rTie, rU, &ncand_s,
+                                              fallbacks, sb_off);
         if (threadIdx.x == 0) keys += nc;
-        // exact keys of the candidates (row index r in the low bits -> slot)
-        const uint32_t *cand = L.cand + (int64_t)sec * L.cand_cap * 2;
-        unsigned long long *ck = L.ckey + (int64_t)sec * L.cand_cap;
-        for (uint32_t q0 = 0; q0 < nc; q0 += PAIR_CAP) {
-            const uint32_t cnt = min((uint32_t)PAIR_CAP, nc - q0);
-            __syncthreads();
-            for (uint32_t c = threadIdx.x; c < cnt; c += blockDim.x) {
-                sm.pi[c] = crow[cand[2 * (q0 + c)] & 0xffu];
-                sm.pj[c] = (int32_t)cand[2 * (q0 + c) + 1];
-            }
-            __syncthreads();
-            block_keys(L, ro, sm.pi, sm.pj, sm.pkey, (int)cnt);
-            __syncthreads();
-            for (uint32_t c = threadIdx.x; c < cnt; c += blockDim.x) ck[q0 + c] = sm.pkey[c];
-        }
-        __syncthreads();
-        // own minima: key, then slot pair
-        for (uint32_t c = threadIdx.x; c < nc; c += blockDim.x)
-            if (cand[2 * c] & 0x40000000u) atomicMin(&rK[cand[2 * c] & 0xffu], ck[c]);
-        __syncthreads();
-        if (threadIdx.x < nr && rK[threadIdx.x] != rU[threadIdx.x]) rTie[threadIdx.x] = ~0ull;
-        __syncthreads();
-        for (uint32_t c = threadIdx.x; c < nc; c += blockDim.x) {
-            const uint32_t w0 = cand[2 * c];
-            const int r = (int)(w0 & 0xffu);
-            if ((w0 & 0x40000000u) && ck[c] == rK[r]) atomicMin(&rTie[r], inc_pack_pair(crow[r], (int)cand[2 * c + 1]));
-        }
-        __syncthreads();
-        if (threadIdx.x < nr) {
-            const int r = threadIdx.x, s = crow[r];
-            const unsigned long long p = rTie[r];
-            L.sbK[ro + s] = rK[r];
-            if (rK[r] == RHSEG_KEY_NONE || p == ~0ull) {
-                L.sbP[ro + s] = -1;
-            } else {
-                const uint32_t lo = (uint32_t)(p >> 32), hi = (uint32_t)p;
-                L.sbP[ro + s] = (int32_t)(lo == (uint32_t)s ? hi : lo);
-            }
-        }
-        __syncthreads();
-        // pushes of the merged rows' keys, one merged row at a time (each
-        // partner appears once per merged row)
-        for (int r = 0; r < nprop; r++) {
-            const int a = crow[r];
-            for (uint32_t c = threadIdx.x; c < nc; c += blockDim.x) {
-                const uint32_t w0 = cand[2 * c];
-                if ((int)(w0 & 0xffu) != r || !(w0 & 0x80000000u)) continue;
-                const int j = (int)cand[2 * c + 1];
-                const uint64_t K = ck[c];
-                const uint64_t oldK = L.sbK[ro + j];
-                const int op = L.sbP[ro + j];
-                const bool better = (oldK == RHSEG_KEY_NONE) ||
-                                    pk_less(pk_make(K, j, a), pk_make(oldK, j, op < 0 ? j : op));
-                if (better) { L.sbK[ro + j] = K; L.sbP[ro + j] = a; }
-            }
-            __syncthreads();
-        }
     }
     __syncthreads();
     for (int k = threadIdx.x; k < nrows; k += blockDim.x) L.inR[ro + R[k]] = 0;
-    keys = block_sum_ll(keys, sm.ll);
     if (threadIdx.x == 0) {
-        stg->npm = 0;
         stg->cands += keys;
-        stg->fallbacks = st.fallbacks;
-        stg->screened += (int64_t)nrows * st.count;     // row x position evaluations of this update
-        stg->cands_true += nrows;                        // rows recomputed
+        stg->fallbacks += fallbacks;
+        stg->screened += (int64_t)nrows * stg->count;     // row x position evaluations of this update
+        stg->cands_true += nrows;                         // rows recomputed
     }
 }
 
