@@ -232,10 +232,12 @@ def main():
     scr_ms = sum(s["screen_ms"] for s in stats)
     scr_n = sum(s["screen_launches"] for s in stats)
     scr_pairs = sum(s["screened_pairs"] for s in stats)
+    # pairs the screen's MMAs actually covered (units proven empty are skipped)
+    scr_eval = sum(s.get("screen_evaluated", 0) for s in stats)
     run_ms = sum(s["run_ms"] for s in stats)
     B = w.bands
     prec = params["precision"]
-    flops = 2.0 * B * scr_pairs
+    flops = 2.0 * B * (scr_eval if scr_eval > 0 else scr_pairs)
     achieved = flops / (scr_ms / 1000.0) / 1e12 if scr_ms > 0 else 0.0
     impl = stats[-1]["screen_impl"]
     if impl == 3:
@@ -271,7 +273,8 @@ def main():
         "screen": {"screened_pairs": stats[-1]["screened_pairs"], "candidates": stats[-1]["candidates"],
                    "candidate_fraction": stats[-1]["candidates"] / max(1, stats[-1]["screened_pairs"]),
                    "candidates_below_threshold": stats[-1]["candidates_below"],
-                   "fallbacks": stats[-1]["fallbacks"]},
+                   "fallbacks": stats[-1]["fallbacks"],
+                   "evaluated_pairs": stats[-1].get("screen_evaluated", 0)},
         "level_ms": [round(x, 2) for x in stats[-1]["level_ms"][:params["rnb_levels"]]],
         "level_iters": stats[-1]["level_iters"][:params["rnb_levels"]],
         "level_kernel_ms": {k: [round(x, 1) for x in stats[-1]["level_" + k + "_ms"][:params["rnb_levels"]]]

@@ -129,6 +129,9 @@ typedef struct rhseg_stats {
     double  level_screen_ms[6], level_adj_ms[6], level_spec_ms[6];
                               /* per level split of screen_ms, adj_ms, spec_ms
                                  (profile = 1 only)                               */
+    int64_t screen_evaluated; /* pairs the tensor-core screen's MMAs actually covered
+                                 (whole 128x256 units; units whose norm ranges prove
+                                 every pair's key >= the threshold are skipped)    */
 } rhseg_stats;
 
 typedef struct rhseg_handle rhseg_handle;

@@ -44,6 +44,7 @@ class Stats(C.Structure):
         ("screen_impl", C.c_int32), ("pad", C.c_int32),
         ("level_ms", C.c_double * 6), ("level_iters", C.c_int32 * 6),
         ("level_screen_ms", C.c_double * 6), ("level_adj_ms", C.c_double * 6), ("level_spec_ms", C.c_double * 6),
+        ("screen_evaluated", C.c_int64),
     ]
 
 

@@ -152,6 +152,9 @@ struct rhseg_handle {
     DBuf<unsigned long long> stie, sinit, ckey;
     DBuf<uint8_t> inR;
     DBuf<float> sT, sE, sk, sbuf, srowx;
+    DBuf<float> nlo, nhi, blo, bhi, bkm;
+    DBuf<int32_t> ulist;
+    DBuf<unsigned long long> sortk;
     DBuf<IncInfo> sinfo;
     // per level, sized at run time
     DBuf<uint32_t> adj;
@@ -418,8 +421,17 @@ static int common_create(rhseg_handle *h, const rhseg_params *p, void *stream)
         if ((rc = h->Af.alloc(h->npos))) return rc;
         if ((rc = h->kf.alloc(h->npos))) return rc;
     }
-    if ((p->precision == 1 || p->precision == 2) && !p->incremental)
+    if ((p->precision == 1 || p->precision == 2) && !p->incremental) {
         if ((rc = h->H.alloc(h->npos))) return rc;
+        // certified norm ranges of the operand rows: units proven empty are skipped
+        if ((rc = h->nlo.alloc(h->npos))) return rc;
+        if ((rc = h->nhi.alloc(h->npos))) return rc;
+        if ((rc = h->sk.alloc(h->npos))) return rc;
+        if ((rc = h->blo.alloc(h->npos / 128 + 1))) return rc;
+        if ((rc = h->bhi.alloc(h->npos / 128 + 1))) return rc;
+        if ((rc = h->bkm.alloc(h->npos / 128 + 1))) return rc;
+        if ((rc = h->sortk.alloc(2 * P))) return rc;
+    }
     if (p->incremental) {
         if ((rc = h->sbK.alloc(P))) return rc;
         if ((rc = h->sbP.alloc(P))) return rc;
@@ -787,6 +799,10 @@ static int run_impl(rhseg_handle *h)
         const bool inc = h->p.incremental && h->p.spclust_wght > 0.0;
         if (inc)
             if ((rc = h->ckey.alloc((size_t)G.nsec * cand_cap))) return rc;
+        const bool skip_units = h->nlo.p != nullptr && h->p.spclust_wght > 0.0;
+        const int32_t ucap = (int32_t)tc_section_units(m0max) + 1;
+        if (skip_units)
+            if ((rc = h->ulist.alloc((size_t)G.nsec * ucap))) return rc;
         CK(cudaMemcpyAsync(h->aoff.p, aoff.data(), 8 * (G.nsec + 1), cudaMemcpyHostToDevice, s));
         CK(cudaMemcpyAsync(h->Wrow.p, W.data(), 4 * G.nsec, cudaMemcpyHostToDevice, s));
         CK(cudaMemsetAsync(h->adj.p, 0, (size_t)atot * 4, s));
@@ -811,6 +827,11 @@ static int run_impl(rhseg_handle *h)
         D.H = (h->p.precision == 1 || h->p.precision == 2) ? h->H.p : nullptr;
         D.adj = h->adj.p; D.cand = h->cand.p; D.cand_cap = cand_cap;
         D.log = h->log.p; D.err = h->err.p;
+        if (skip_units) {
+            D.nlo = h->nlo.p; D.nhi = h->nhi.p; D.sk = h->sk.p;
+            D.blo = h->blo.p; D.bhi = h->bhi.p; D.bkm = h->bkm.p;
+            D.ulist = h->ulist.p; D.ucap = ucap; D.sortk = h->sortk.p;
+        }
         if (inc) {
             D.H = nullptr;
             D.incremental = 1;
@@ -824,6 +845,10 @@ static int run_impl(rhseg_handle *h)
         k_init_section<<<G.nsec, STEP_THREADS, 0, s>>>(D, sc, target); h->nlaunch++;
         if (h->p.spclust_wght > 0.0) {
             k_write_rows<<<dim3(16, G.nsec), 256, 0, s>>>(D, sc); h->nlaunch++;
+            if (skip_units) {             // positions in norm order, rows rewritten there
+                k_sort_positions<<<G.nsec, STEP_THREADS, 0, s>>>(D); h->nlaunch++;
+                k_write_rows<<<dim3(16, G.nsec), 256, 0, s>>>(D, sc); h->nlaunch++;
+            }
         }
         CK(cudaGetLastError());
         if (inc) {
@@ -911,6 +936,7 @@ static int run_impl(rhseg_handle *h)
             h->stats.pairs += q.pairs;
             h->stats.iterations += q.iter;
             h->stats.screened_pairs += q.screened;
+            h->stats.screen_evaluated += q.evaluated;
             h->stats.candidates += q.cands;
             h->stats.candidates_below += q.cands_true;
             h->stats.fallbacks += q.fallbacks;
@@ -1212,6 +1238,8 @@ extern "C" void rhseg_destroy(rhseg_handle *h)
     h->slots[0].release(); h->slots[1].release();
     h->sbK.release(); h->sbP.release(); h->srow.release(); h->stie.release(); h->sinit.release();
     h->ckey.release(); h->inR.release(); h->sT.release(); h->sE.release(); h->sk.release(); h->sbuf.release();
+    h->nlo.release(); h->nhi.release(); h->blo.release(); h->bhi.release(); h->bkm.release(); h->ulist.release();
+    h->sortk.release();
     h->srowx.release(); h->sinfo.release();
     h->slot_of_pos.release(); h->X.release(); h->Af.release(); h->kf.release(); h->H.release(); h->Ad.release(); h->kd.release();
     h->adj.release(); h->aoff.release(); h->Wrow.release(); h->ref.release(); h->cand.release(); h->st.release();

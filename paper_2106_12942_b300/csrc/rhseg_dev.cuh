@@ -38,6 +38,8 @@ struct SecState {
     int32_t rows_from;     // > 0: the position list was rebuilt this iteration (old extent)
     int32_t pm_a[2], pm_b[2];   // incremental mode: merges (survivor, absorbed) whose rows are pending
     int32_t npm;
+    int32_t nunits;        // tensor-core screen: units kept for this step (the rest are proven empty)
+    int64_t evaluated;     // pairs covered by the kept units, accumulated
 };
 
 // Geometry and buffers of the level in flight (device pointers).  Arrays
@@ -91,6 +93,11 @@ struct LevelDev {
     unsigned long long *sinit; // per position: approximate argmin, then the row's bound
     float *sT;                 // per position: the row's binary32 threshold
     float *sE, *sk;            // per position: operand error norm, 4^-sigma / n (both rounded up)
+    float *nlo, *nhi;          // per position: bounds of the true norm ||x|| of the row (tensor-core screen)
+    float *blo, *bhi, *bkm;    // per 128-position block: min nlo, max nhi, max k of its live rows
+    int32_t *ulist;            // [nsec][ucap] kept units of the step, (I << 16) | Jp
+    int32_t ucap;
+    unsigned long long *sortk; // per slot x 2: scratch of the norm-order sort of the positions
     float inc_onepg;           // 1 + gamma_B for a binary32 sum of Bpad non-negative terms (rounded up)
     float *sbuf;               // per position x 8: scratch (sums of squared differences of a row update)
     float *srowx;              // per section: staged row vectors of a row update [Bpad][8]
@@ -249,6 +256,22 @@ __device__ __forceinline__ double warp_key(const int64_t *__restrict__ Si, int64
 __device__ __forceinline__ uint64_t dbits(double x) { return (uint64_t)__double_as_longlong(x); }
 
 // Packed (K bits, lo slot, hi slot) comparisons.
+// Decode a local upper-triangle tile index into (I, J), I <= J < nb
+// (binary32 estimate, exact integer correction; no FP64 instruction).
+__device__ __forceinline__ void tri_decode(long long local, long long nb, int &I, int &J)
+{
+    float a = 2.0f * (float)(int)nb + 1.0f;                 // 32-bit conversions only
+    float disc = fmaxf(a * a - 8.0f * (float)(int)local, 0.0f);
+    long long i = (long long)((a - sqrtf(disc)) * 0.5f);
+    if (i < 0) i = 0;
+    if (i > nb - 1) i = nb - 1;
+    while (i > 0 && i * nb - i * (i - 1) / 2 > local) i--;
+    while (i + 1 < nb && (i + 1) * nb - (i + 1) * i / 2 <= local) i++;
+    long long off = i * nb - i * (i - 1) / 2;
+    I = (int)i;
+    J = (int)(i + (local - off));
+}
+
 struct PairKey { uint64_t k; uint32_t lo, hi; };
 
 __device__ __forceinline__ bool pk_less(const PairKey &a, const PairKey &b)

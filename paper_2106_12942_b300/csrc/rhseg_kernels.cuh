@@ -339,11 +339,18 @@ __device__ void warp_write_row(const LevelDev &L, int sec, int slot, int pos, co
     if (lane == 0) {
         L.Af[L.poff[sec] + pos] = __fmaf_rd(q, sc.Fq, -sc.E0);
         L.kf[L.poff[sec] + pos] = __fdiv_ru(sc.kscale_f, __int2float_rd((int)n));
-        if (L.sE != nullptr) {
-            // operand error norm and 4^-sigma/n for the incremental minima's key bound
-            const float e = __fadd_ru(__fmul_ru(sc.u_f, __fsqrt_ru(__fmul_ru(q, sc.onepg_f))), sc.etaB_f);
-            L.sE[L.poff[sec] + pos] = __fmul_ru(e, 1.0f + 0x1p-20f);
-            L.sk[L.poff[sec] + pos] = __fdiv_ru(sc.k1_f, __int2float_rd((int)n));
+        if (L.sE != nullptr || L.nlo != nullptr) {
+            // operand error norm e >= ||x^ - x|| and 4^-sigma/n (rounded up)
+            const float e = __fmul_ru(__fadd_ru(__fmul_ru(sc.u_f, __fsqrt_ru(__fmul_ru(q, sc.onepg_f))), sc.etaB_f),
+                                      1.0f + 0x1p-20f);
+            const float kp = __fdiv_ru(sc.k1_f, __int2float_rd((int)n));
+            if (L.sE != nullptr) L.sE[L.poff[sec] + pos] = e;
+            L.sk[L.poff[sec] + pos] = kp;
+            if (L.nlo != nullptr) {
+                // bounds of the true norm: ||x^|| within sqrt(q (1 +- gamma_B)), then +- e
+                L.nlo[L.poff[sec] + pos] = fmaxf(0.0f, __fsub_rd(__fsqrt_rd(__fdiv_rd(q, sc.onepg_f)), e));
+                L.nhi[L.poff[sec] + pos] = __fadd_ru(__fsqrt_ru(__fmul_ru(q, sc.onepg_f)), e);
+            }
         }
     }
 }
@@ -406,6 +413,7 @@ __global__ void __launch_bounds__(STEP_THREADS) k_init_section(LevelDev L, Scree
         st->rows_from = m0;
         st->npm = 0;
         st->ncand = 0;
+        st->nunits = 0;
         st->done = (m0 <= target) ? 1 : 0;
         st->Kadj = __longlong_as_double(0x7FF0000000000000ll);
         st->tthr = st->Kadj;
@@ -743,10 +751,102 @@ __device__ void block_merge(const LevelDev &L, int sec, SecState &st, int a, int
     __syncthreads();
 }
 
+// New position list of the live slots in order of their rows' certified
+// norms (the tensor-core screen then finds whole units of pairs far apart in
+// norm, which its norm bound proves to be above the threshold).  Bitonic
+// sort of (norm bits, slot) in the section's scratch (whole block); the
+// operand rows are then rewritten by k_write_rows.
+__device__ void block_sort_positions(const LevelDev &L, int sec, SecState &st)
+{
+    const int m0 = st.m0;
+    const int64_t ro = L.roff[sec], pb = L.poff[sec];
+    unsigned long long *a = L.sortk + 2 * ro;
+    int n2 = 1;
+    while (n2 < m0) n2 <<= 1;
+    __shared__ int32_t nlive;
+    if (threadIdx.x == 0) nlive = 0;
+    __syncthreads();
+    for (int i = threadIdx.x; i < n2; i += blockDim.x) {
+        unsigned long long v = ~0ull;
+        if (i < m0 && L.alive[ro + i]) {
+            const float nr = L.nhi[pb + L.pos_of_slot[ro + i]];             // >= 0: bits order as floats
+            v = ((unsigned long long)(uint32_t)__float_as_int(nr) << 32) | (uint32_t)i;
+            atomicAdd(&nlive, 1);
+        }
+        a[i] = v;
+    }
+    __syncthreads();
+    for (int k = 2; k <= n2; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = threadIdx.x; i < n2; i += blockDim.x) {
+                const int ixj = i ^ j;
+                if (ixj > i) {
+                    const unsigned long long x = a[i], y = a[ixj];
+                    if ((x > y) == ((i & k) == 0)) { a[i] = y; a[ixj] = x; }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    const int n = nlive;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const int slot = (int)(uint32_t)a[i];
+        L.pos_of_slot[ro + slot] = i;
+        L.slot_of_pos[pb + i] = slot;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        st.rows_from = max(st.mc, 1);   // old extent: positions past the new end are marked dead
+        st.mc = n;
+    }
+    __syncthreads();
+}
+
+// Compaction that keeps the live positions in their current order (the norm
+// order set at level start; a merged region keeps its position, its new
+// norm close to its parts'), in place (new positions never exceed old ones).
+__device__ void block_compact_in_order(const LevelDev &L, int sec, SecState &st)
+{
+    const int mc = st.mc;
+    const int64_t ro = L.roff[sec], pb = L.poff[sec];
+    __shared__ int32_t wcnt[32];
+    __shared__ int32_t base;
+    if (threadIdx.x == 0) base = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int c = 0; c < mc; c += blockDim.x) {
+        const int p = c + threadIdx.x;
+        const int slot = (p < mc) ? L.slot_of_pos[pb + p] : -1;
+        const int f = (slot >= 0) ? L.alive[ro + slot] : 0;
+        const unsigned bal = __ballot_sync(0xffffffffu, f);
+        if (lane == 0) wcnt[wid] = __popc(bal);
+        __syncthreads();
+        int off = 0, tot = 0;
+        for (int k = 0; k < nw; k++) { if (k < wid) off += wcnt[k]; tot += wcnt[k]; }
+        if (f) {
+            const int np = base + off + __popc(bal & ((1u << lane) - 1));
+            L.pos_of_slot[ro + slot] = np;
+            L.slot_of_pos[pb + np] = slot;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) base += tot;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        st.rows_from = st.mc;       // old extent: positions past the new end are marked dead
+        st.mc = base;
+    }
+    __syncthreads();
+}
+
 // New stable position list of the live slots (the screen's operand rows are
 // then rewritten by k_write_rows).
 __device__ void block_compact_positions(const LevelDev &L, int sec, SecState &st)
 {
+    if (L.sortk != nullptr) {
+        block_compact_in_order(L, sec, st);
+        return;
+    }
     const int m0 = st.m0;
     const int64_t ro = L.roff[sec];
     __shared__ int32_t wcnt[32];
@@ -794,6 +894,92 @@ __global__ void __launch_bounds__(256) k_write_rows(LevelDev L, ScreenConst sc)
     for (int pos = gw; pos < mc; pos += ngw) write_row_any(L, sec, L.slot_of_pos[L.poff[sec] + pos], pos, sc);
     for (int pos = mc + blockIdx.x * blockDim.x + threadIdx.x; pos < pend; pos += gridDim.x * blockDim.x)
         mark_pos_dead(L, sec, pos);
+}
+
+// Units of this step's tensor-core screen that may hold a pair with K < t
+// (whole block).  For rows i, j: ||x_i - x_j|| >= | ||x_i|| - ||x_j|| |, so
+// every pair of 128-position blocks b, c has K >= gap(b, c)^2 / (kmax_b +
+// kmax_c), gap being the distance between the blocks' certified norm
+// ranges; a unit (I, Jp) is dropped when that bound is >= t for both of its
+// column blocks 2 Jp, 2 Jp + 1 (all in binary32, rounded to the safe side).
+// The kept units are listed in order; their count and covered pairs go to st.
+__device__ void block_unit_list(const LevelDev &L, int sec, SecState &st, float Tf)
+{
+    const int mc = st.mc;
+    const int64_t pb = L.poff[sec];
+    const int64_t bb = pb / 128;
+    const int nb = (mc + 127) / 128, nbp = (nb + 1) / 2;
+    const int wid = threadIdx.x >> 5, nw = blockDim.x >> 5, lane = threadIdx.x & 31;
+    const float inf = __int_as_float(0x7f800000);
+    for (int b = wid; b < nb; b += nw) {
+        float lo = inf, hi = -inf, km = 0.0f;
+        for (int e = lane; e < 128; e += 32) {
+            const int pos = b * 128 + e;
+            if (pos >= mc || !(L.Af[pb + pos] < inf)) continue;       // dead or past the end
+            lo = fminf(lo, L.nlo[pb + pos]);
+            hi = fmaxf(hi, L.nhi[pb + pos]);
+            km = fmaxf(km, L.sk[pb + pos]);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+            hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+            km = fmaxf(km, __shfl_xor_sync(0xffffffffu, km, o));
+        }
+        if (lane == 0) { L.blo[bb + b] = lo; L.bhi[bb + b] = hi; L.bkm[bb + b] = km; }
+    }
+    __syncthreads();
+    const int total = nbp * (nbp + 1) - (nb & 1);
+    __shared__ int32_t wsum[32];
+    __shared__ int32_t base;
+    if (threadIdx.x == 0) base = 0;
+    __syncthreads();
+    int32_t *ul = L.ulist + (int64_t)sec * L.ucap;
+    for (int u0 = 0; u0 < total; u0 += blockDim.x) {
+        const int u = u0 + threadIdx.x;
+        bool keep = false;
+        int I = 0, Jp = 0;
+        if (u < total) {
+            int Ip;
+            tri_decode(u >> 1, nbp, Ip, Jp);
+            I = 2 * Ip + (u & 1);
+            for (int h = 0; h < 2 && !keep; h++) {
+                const int J = 2 * Jp + h;
+                if (J >= nb) continue;
+                const float gap = fmaxf(0.0f, fmaxf(__fsub_rd(L.blo[bb + J], L.bhi[bb + I]),
+                                                    __fsub_rd(L.blo[bb + I], L.bhi[bb + J])));
+                const float klo = __fdiv_rd(__fmul_rd(gap, gap), __fadd_ru(L.bkm[bb + I], L.bkm[bb + J]));
+                keep = !(klo >= Tf);                 // NaN (no live rows) keeps nothing: inf gap
+            }
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, keep);
+        if (lane == 0) wsum[wid] = __popc(bal);
+        __syncthreads();
+        int off = 0, tot = 0;
+        for (int k = 0; k < nw; k++) { if (k < wid) off += wsum[k]; tot += wsum[k]; }
+        if (keep) ul[base + off + __popc(bal & ((1u << lane) - 1))] = (I << 16) | Jp;
+        __syncthreads();
+        if (threadIdx.x == 0) base += tot;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        st.nunits = base;
+        st.evaluated += (int64_t)base * 128 * 256;
+    }
+}
+
+// Level start with the norm-ordered screen: the positions in norm order,
+// once the first operand rows (identity positions) exist.
+__global__ void __launch_bounds__(STEP_THREADS) k_sort_positions(LevelDev L)
+{
+    const int sec = blockIdx.x;
+    if (sec >= L.nsec) return;
+    __shared__ SecState st;
+    if (threadIdx.x == 0) st = L.st[sec];
+    __syncthreads();
+    if (st.done) return;
+    block_sort_positions(L, sec, st);
+    if (threadIdx.x == 0) L.st[sec] = st;
 }
 
 // Step 2 of HSEG: merge the adjacent pair of minimum key.
@@ -863,6 +1049,7 @@ __global__ void __launch_bounds__(STEP_THREADS, 2) k_adj_step(LevelDev L, Screen
         const float inf = __int_as_float(0x7f800000);
         for (int pos = threadIdx.x; pos < pend; pos += blockDim.x)
             L.H[pb + pos] = (pos < mc) ? 0.5f * (L.Af[pb + pos] - Tf * L.kf[pb + pos]) : inf;
+        if (L.ulist != nullptr) block_unit_list(L, sec, st, Tf);
     }
     __syncthreads();
     if (threadIdx.x == 0) L.st[sec] = st;

@@ -52,7 +52,7 @@ __device__ void block_tile_prefix(const LevelDev &L, int tile, long long *pre)
                 }
             } else if (st.spec_pending && st.tthr < __longlong_as_double(0x7FF0000000000000ll)) {
                 if (tile == 0) {
-                    t = tc_section_units(st.mc);
+                    t = (L.ulist != nullptr) ? st.nunits : tc_section_units(st.mc);
                 } else {
                     long long nb = (st.mc + tile - 1) / tile;
                     t = nb * (nb + 1) / 2;
@@ -83,22 +83,6 @@ __device__ void block_tile_prefix(const LevelDev &L, int tile, long long *pre)
     }
     if (threadIdx.x == 0) pre[nsec] = tot;
     __syncthreads();
-}
-
-// Decode a local upper-triangle tile index into (I, J), I <= J < nb
-// (binary32 estimate, exact integer correction; no FP64 instruction).
-__device__ __forceinline__ void tri_decode(long long local, long long nb, int &I, int &J)
-{
-    float a = 2.0f * (float)(int)nb + 1.0f;                 // 32-bit conversions only
-    float disc = fmaxf(a * a - 8.0f * (float)(int)local, 0.0f);
-    long long i = (long long)((a - sqrtf(disc)) * 0.5f);
-    if (i < 0) i = 0;
-    if (i > nb - 1) i = nb - 1;
-    while (i > 0 && i * nb - i * (i - 1) / 2 > local) i--;
-    while (i + 1 < nb && (i + 1) * nb - (i + 1) * i / 2 <= local) i++;
-    long long off = i * nb - i * (i - 1) / 2;
-    I = (int)i;
-    J = (int)(i + (local - off));
 }
 
 __device__ __forceinline__ int find_section(const long long *pre, int nsec, long long t)

@@ -267,7 +267,7 @@ struct TcJob {
 // unit (units are visited in increasing order, so the section only moves
 // forward); the per-section data come from shared memory.
 __device__ __forceinline__ bool tc_unit(const TcShared &sh, const TcJob &job, long long t, long long total, int &cursor,
-                                        TcUnit &u)
+                                        TcUnit &u, const int32_t *L_ulist = nullptr, int L_ucap = 0)
 {
     if (t >= total) return false;
     if (job.gram_rows > 0) {
@@ -284,10 +284,16 @@ __device__ __forceinline__ bool tc_unit(const TcShared &sh, const TcJob &job, lo
     cursor = s;
     u.sec = s;
     const long long local = t - sh.pre[s];
-    const long long nb = (sh.smc[s] + TC_TILE - 1) / TC_TILE, nbp = (nb + 1) / 2;
-    int Ip;
-    tri_decode(local >> 1, nbp, Ip, u.Jp);
-    u.I = 2 * Ip + (int)(local & 1);
+    if (L_ulist != nullptr) {                    // the step's kept units, listed per section
+        const int32_t e = L_ulist[(int64_t)s * L_ucap + local];
+        u.I = e >> 16;
+        u.Jp = e & 0xffff;
+    } else {
+        const long long nb = (sh.smc[s] + TC_TILE - 1) / TC_TILE, nbp = (nb + 1) / 2;
+        int Ip;
+        tri_decode(local >> 1, nbp, Ip, u.Jp);
+        u.I = 2 * Ip + (int)(local & 1);
+    }
     u.rowA = sh.spoff[s] + (int64_t)u.I * TC_TILE;
     u.rowB = sh.spoff[s] + (int64_t)u.Jp * TC_N;
     return true;
@@ -371,7 +377,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_screen_tc(LevelDev L, const _
                 const int kc = (int)(c - k * natoms);
                 const int slot = (int)(c % TC_STAGES);
                 if (k != kdec) {
-                    tc_unit(sh, job, blockIdx.x + k * gridDim.x, total, cursor, u);
+                    tc_unit(sh, job, blockIdx.x + k * gridDim.x, total, cursor, u, job.gram_rows > 0 ? nullptr : L.ulist,
+                            L.ucap);
                     kdec = k;
                 }
                 if (kc == 0) {
