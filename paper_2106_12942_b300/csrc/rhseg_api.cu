@@ -152,7 +152,7 @@ struct rhseg_handle {
     DBuf<unsigned long long> stie, sinit, ckey;
     DBuf<uint8_t> inR;
     DBuf<float> sT, sE, sk, sbuf, srowx;
-    DBuf<float> nlo, nhi, blo, bhi, bkm;
+    DBuf<float> nlo, nhi;
     DBuf<int32_t> ulist;
     DBuf<unsigned long long> sortk;
     DBuf<IncInfo> sinfo;
@@ -427,9 +427,6 @@ static int common_create(rhseg_handle *h, const rhseg_params *p, void *stream)
         if ((rc = h->nlo.alloc(h->npos))) return rc;
         if ((rc = h->nhi.alloc(h->npos))) return rc;
         if ((rc = h->sk.alloc(h->npos))) return rc;
-        if ((rc = h->blo.alloc(h->npos / 128 + 1))) return rc;
-        if ((rc = h->bhi.alloc(h->npos / 128 + 1))) return rc;
-        if ((rc = h->bkm.alloc(h->npos / 128 + 1))) return rc;
         if ((rc = h->sortk.alloc(2 * P))) return rc;
     }
     if (p->incremental) {
@@ -829,7 +826,6 @@ static int run_impl(rhseg_handle *h)
         D.log = h->log.p; D.err = h->err.p;
         if (skip_units) {
             D.nlo = h->nlo.p; D.nhi = h->nhi.p; D.sk = h->sk.p;
-            D.blo = h->blo.p; D.bhi = h->bhi.p; D.bkm = h->bkm.p;
             D.ulist = h->ulist.p; D.ucap = ucap; D.sortk = h->sortk.p;
         }
         if (inc) {
@@ -844,10 +840,10 @@ static int run_impl(rhseg_handle *h)
         int32_t target = (lev == 1) ? h->p.conv_nregions : h->min_nr;
         k_init_section<<<G.nsec, STEP_THREADS, 0, s>>>(D, sc, target); h->nlaunch++;
         if (h->p.spclust_wght > 0.0) {
-            k_write_rows<<<dim3(16, G.nsec), 256, 0, s>>>(D, sc); h->nlaunch++;
+            k_write_rows<<<dim3(64, G.nsec), 256, 0, s>>>(D, sc); h->nlaunch++;
             if (skip_units) {             // positions in norm order, rows rewritten there
                 k_sort_positions<<<G.nsec, STEP_THREADS, 0, s>>>(D); h->nlaunch++;
-                k_write_rows<<<dim3(16, G.nsec), 256, 0, s>>>(D, sc); h->nlaunch++;
+                k_write_rows<<<dim3(64, G.nsec), 256, 0, s>>>(D, sc); h->nlaunch++;
             }
         }
         CK(cudaGetLastError());
@@ -894,7 +890,7 @@ static int run_impl(rhseg_handle *h)
                     if (inc) k_spec_inc<<<G.nsec, STEP_THREADS, 0, s>>>(D, sc);
                     else k_spec_step<<<G.nsec, STEP_THREADS, 0, s>>>(D, sc);
                     h->nlaunch++;
-                    k_write_rows<<<dim3(16, G.nsec), 256, 0, s>>>(D, sc); h->nlaunch++;
+                    k_write_rows<<<dim3(64, G.nsec), 256, 0, s>>>(D, sc); h->nlaunch++;
                     if (prof) CK(cudaEventRecord(h->prof_ev[(2 * chunk + k) * 2 + 1], s));
                 }
             }
@@ -1238,7 +1234,7 @@ extern "C" void rhseg_destroy(rhseg_handle *h)
     h->slots[0].release(); h->slots[1].release();
     h->sbK.release(); h->sbP.release(); h->srow.release(); h->stie.release(); h->sinit.release();
     h->ckey.release(); h->inR.release(); h->sT.release(); h->sE.release(); h->sk.release(); h->sbuf.release();
-    h->nlo.release(); h->nhi.release(); h->blo.release(); h->bhi.release(); h->bkm.release(); h->ulist.release();
+    h->nlo.release(); h->nhi.release(); h->ulist.release();
     h->sortk.release();
     h->srowx.release(); h->sinfo.release();
     h->slot_of_pos.release(); h->X.release(); h->Af.release(); h->kf.release(); h->H.release(); h->Ad.release(); h->kd.release();

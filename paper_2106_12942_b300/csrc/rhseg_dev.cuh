@@ -94,7 +94,6 @@ struct LevelDev {
     float *sT;                 // per position: the row's binary32 threshold
     float *sE, *sk;            // per position: operand error norm, 4^-sigma / n (both rounded up)
     float *nlo, *nhi;          // per position: bounds of the true norm ||x|| of the row (tensor-core screen)
-    float *blo, *bhi, *bkm;    // per 128-position block: min nlo, max nhi, max k of its live rows
     int32_t *ulist;            // [nsec][ucap] kept units of the step, (I << 16) | Jp
     int32_t ucap;
     unsigned long long *sortk; // per slot x 2: scratch of the norm-order sort of the positions

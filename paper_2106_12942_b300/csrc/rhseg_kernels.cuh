@@ -903,61 +903,81 @@ __global__ void __launch_bounds__(256) k_write_rows(LevelDev L, ScreenConst sc)
 // ranges; a unit (I, Jp) is dropped when that bound is >= t for both of its
 // column blocks 2 Jp, 2 Jp + 1 (all in binary32, rounded to the safe side).
 // The kept units are listed in order; their count and covered pairs go to st.
+constexpr int UL_MAX_BLOCKS = 512;     // sections of up to 65536 positions skip units; larger keep all
+
 __device__ void block_unit_list(const LevelDev &L, int sec, SecState &st, float Tf)
 {
     const int mc = st.mc;
     const int64_t pb = L.poff[sec];
-    const int64_t bb = pb / 128;
     const int nb = (mc + 127) / 128, nbp = (nb + 1) / 2;
     const int wid = threadIdx.x >> 5, nw = blockDim.x >> 5, lane = threadIdx.x & 31;
     const float inf = __int_as_float(0x7f800000);
-    for (int b = wid; b < nb; b += nw) {
-        float lo = inf, hi = -inf, km = 0.0f;
-        for (int e = lane; e < 128; e += 32) {
-            const int pos = b * 128 + e;
-            if (pos >= mc || !(L.Af[pb + pos] < inf)) continue;       // dead or past the end
-            lo = fminf(lo, L.nlo[pb + pos]);
-            hi = fmaxf(hi, L.nhi[pb + pos]);
-            km = fmaxf(km, L.sk[pb + pos]);
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, o));
-            hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, o));
-            km = fmaxf(km, __shfl_xor_sync(0xffffffffu, km, o));
-        }
-        if (lane == 0) { L.blo[bb + b] = lo; L.bhi[bb + b] = hi; L.bkm[bb + b] = km; }
-    }
-    __syncthreads();
-    const int total = nbp * (nbp + 1) - (nb & 1);
+    __shared__ float blo[UL_MAX_BLOCKS], bhi[UL_MAX_BLOCKS], bkm[UL_MAX_BLOCKS];
     __shared__ int32_t wsum[32];
     __shared__ int32_t base;
+    const bool ranges = nb <= UL_MAX_BLOCKS;
+    if (ranges) {
+        for (int b = wid; b < nb; b += nw) {
+            float lo = inf, hi = -inf, km = 0.0f;
+            for (int e = lane; e < 128; e += 32) {
+                const int pos = b * 128 + e;
+                if (pos >= mc || !(L.Af[pb + pos] < inf)) continue;   // dead or past the end
+                lo = fminf(lo, L.nlo[pb + pos]);
+                hi = fmaxf(hi, L.nhi[pb + pos]);
+                km = fmaxf(km, L.sk[pb + pos]);
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+                hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+                km = fmaxf(km, __shfl_xor_sync(0xffffffffu, km, o));
+            }
+            if (lane == 0) { blo[b] = lo; bhi[b] = hi; bkm[b] = km; }
+        }
+    }
     if (threadIdx.x == 0) base = 0;
     __syncthreads();
+    // tiles (Ip, Jp), Ip <= Jp, in row-major order; each gives the units
+    // (2 Ip, Jp) and (2 Ip + 1, Jp) (the latter only if that row block exists)
     int32_t *ul = L.ulist + (int64_t)sec * L.ucap;
-    for (int u0 = 0; u0 < total; u0 += blockDim.x) {
-        const int u = u0 + threadIdx.x;
-        bool keep = false;
-        int I = 0, Jp = 0;
-        if (u < total) {
-            int Ip;
-            tri_decode(u >> 1, nbp, Ip, Jp);
-            I = 2 * Ip + (u & 1);
-            for (int h = 0; h < 2 && !keep; h++) {
-                const int J = 2 * Jp + h;
-                if (J >= nb) continue;
-                const float gap = fmaxf(0.0f, fmaxf(__fsub_rd(L.blo[bb + J], L.bhi[bb + I]),
-                                                    __fsub_rd(L.blo[bb + I], L.bhi[bb + J])));
-                const float klo = __fdiv_rd(__fmul_rd(gap, gap), __fadd_ru(L.bkm[bb + I], L.bkm[bb + J]));
-                keep = !(klo >= Tf);                 // NaN (no live rows) keeps nothing: inf gap
+    const int ntile = nbp * nbp;
+    for (int t0 = 0; t0 < ntile; t0 += blockDim.x) {
+        const int t = t0 + threadIdx.x;
+        int keep[2] = {0, 0};
+        int Ip = 0, Jp = 0;
+        if (t < ntile) {
+            Ip = t / nbp;
+            Jp = t - Ip * nbp;
+            if (Jp >= Ip) {
+                for (int h = 0; h < 2; h++) {
+                    const int I = 2 * Ip + h;
+                    if (I >= nb) continue;
+                    bool k = !ranges;
+                    for (int c = 0; c < 2 && !k; c++) {
+                        const int J = 2 * Jp + c;
+                        if (J >= nb) continue;
+                        const float gap = fmaxf(0.0f, fmaxf(__fsub_rd(blo[J], bhi[I]), __fsub_rd(blo[I], bhi[J])));
+                        const float klo = __fdiv_rd(__fmul_rd(gap, gap), __fadd_ru(bkm[I], bkm[J]));
+                        k = !(klo >= Tf);                 // empty blocks: infinite gap, dropped
+                    }
+                    keep[h] = k ? 1 : 0;
+                }
             }
         }
-        const unsigned bal = __ballot_sync(0xffffffffu, keep);
-        if (lane == 0) wsum[wid] = __popc(bal);
+        const int cnt = keep[0] + keep[1];
+        int incl = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += v;
+        }
+        if (lane == 31) wsum[wid] = incl;
         __syncthreads();
         int off = 0, tot = 0;
-        for (int k = 0; k < nw; k++) { if (k < wid) off += wsum[k]; tot += wsum[k]; }
-        if (keep) ul[base + off + __popc(bal & ((1u << lane) - 1))] = (I << 16) | Jp;
+        for (int k2 = 0; k2 < nw; k2++) { if (k2 < wid) off += wsum[k2]; tot += wsum[k2]; }
+        int w = base + off + incl - cnt;
+        for (int h = 0; h < 2; h++)
+            if (keep[h]) ul[w++] = ((2 * Ip + h) << 16) | Jp;
         __syncthreads();
         if (threadIdx.x == 0) base += tot;
         __syncthreads();
