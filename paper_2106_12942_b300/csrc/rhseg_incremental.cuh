@@ -251,7 +251,7 @@ __global__ void __launch_bounds__(256) k_sinit_exact(LevelDev L)
 
 // Exact keys of `cnt` (row, partner) slot pairs staged from a section's
 // candidate list, with the keys written back to ckey (whole block).
-__device__ void inc_keys_from_list(const LevelDev &L, int sec, uint32_t c0, uint32_t cnt, StepSmem &sm, bool flip)
+__device__ void inc_keys_from_list(const LevelDev &L, int sec, uint32_t c0, uint32_t cnt, StepSmem &sm)
 {
     const int64_t ro = L.roff[sec];
     const uint32_t *cand = L.cand + (int64_t)sec * L.cand_cap * 2;
@@ -259,8 +259,8 @@ __device__ void inc_keys_from_list(const LevelDev &L, int sec, uint32_t c0, uint
     __syncthreads();
     for (uint32_t c = threadIdx.x; c < cnt; c += blockDim.x) {
         const uint32_t a = cand[2 * (c0 + c)] & 0x3fffffffu, b = cand[2 * (c0 + c) + 1];
-        sm.pi[c] = (int32_t)(flip ? b : a);
-        sm.pj[c] = (int32_t)(flip ? a : b);
+        sm.pi[c] = (int32_t)a;
+        sm.pj[c] = (int32_t)b;
     }
     __syncthreads();
     block_keys(L, ro, sm.pi, sm.pj, sm.pkey, (int)cnt);
@@ -314,7 +314,7 @@ __global__ void __launch_bounds__(STEP_THREADS) k_sinit_final(LevelDev L)
     }
     // keys: each candidate carries flags for the rows it serves (bit 30: row
     // i = cand[0], bit 31: row j = cand[1]); one key serves both
-    for (uint32_t c0 = 0; c0 < ncand; c0 += PAIR_CAP) inc_keys_from_list(L, sec, c0, min((uint32_t)PAIR_CAP, ncand - c0), sm, false);
+    for (uint32_t c0 = 0; c0 < ncand; c0 += PAIR_CAP) inc_keys_from_list(L, sec, c0, min((uint32_t)PAIR_CAP, ncand - c0), sm);
     // phase 1: minimum key per row
     for (uint32_t c = threadIdx.x; c < ncand; c += blockDim.x) {
         const uint32_t w0 = cand[2 * c], j = cand[2 * c + 1], i = w0 & 0x3fffffffu;

@@ -20,12 +20,14 @@
 // columns) and issues tcgen05.mma (M=128, N=256, K=16) from one thread,
 // committing once per group of K slices (each commit costs the tensor pipe
 // about one MMA); warps 5-12 read the accumulator with tcgen05.ld (two
-// warps per 32-lane quarter, 128 columns each) and run the test.  The 128x256 unit carries a
-// third more MMA work per operand byte than a 128x128 tile, which is what
-// the screen is bound by: the operand stream from L2.  Persistent CTAs walk
-// the work units of every pending section.  Every mbarrier wait is bounded;
-// a wait that gives up sets the device error word and all roles leave their
-// loops, so the tensor memory is always released.
+// warps per 32-lane quarter, 128 columns each) and run the test.  An
+// M=128 MMA costs the tensor pipe about the same time for N=128 as for
+// N=256, so the 128x256 unit doubles the work per instruction.  Persistent
+// CTAs walk the units each section lists for the step (units whose
+// certified norm ranges prove every pair's key above the threshold are not
+// listed, see block_unit_list).  Every mbarrier wait is bounded; a wait that
+// gives up sets the device error word and all roles leave their loops, so
+// the tensor memory is always released.
 #pragma once
 #include <cuda.h>
 #include <cuda_fp16.h>
