@@ -840,10 +840,10 @@ static int run_impl(rhseg_handle *h)
         int32_t target = (lev == 1) ? h->p.conv_nregions : h->min_nr;
         k_init_section<<<G.nsec, STEP_THREADS, 0, s>>>(D, sc, target); h->nlaunch++;
         if (h->p.spclust_wght > 0.0) {
-            k_write_rows<<<dim3(64, G.nsec), 256, 0, s>>>(D, sc); h->nlaunch++;
+            k_write_rows<<<h->n_sm * 4, 256, 0, s>>>(D, sc); h->nlaunch++;
             if (skip_units) {             // positions in norm order, rows rewritten there
                 k_sort_positions<<<G.nsec, STEP_THREADS, 0, s>>>(D); h->nlaunch++;
-                k_write_rows<<<dim3(64, G.nsec), 256, 0, s>>>(D, sc); h->nlaunch++;
+                k_write_rows<<<h->n_sm * 4, 256, 0, s>>>(D, sc); h->nlaunch++;
             }
         }
         CK(cudaGetLastError());
@@ -890,7 +890,7 @@ static int run_impl(rhseg_handle *h)
                     if (inc) k_spec_inc<<<G.nsec, STEP_THREADS, 0, s>>>(D, sc);
                     else k_spec_step<<<G.nsec, STEP_THREADS, 0, s>>>(D, sc);
                     h->nlaunch++;
-                    k_write_rows<<<dim3(64, G.nsec), 256, 0, s>>>(D, sc); h->nlaunch++;
+                    k_write_rows<<<h->n_sm * 4, 256, 0, s>>>(D, sc); h->nlaunch++;
                     if (prof) CK(cudaEventRecord(h->prof_ev[(2 * chunk + k) * 2 + 1], s));
                 }
             }

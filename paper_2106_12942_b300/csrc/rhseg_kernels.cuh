@@ -879,21 +879,48 @@ __device__ void block_compact_positions(const LevelDev &L, int sec, SecState &st
 }
 
 // Operand rows of every position of the sections whose position list was
-// (re)built this iteration; many blocks per section, one warp per row.
+// (re)built this iteration.  A single wave of blocks: every block lists those
+// sections (few per iteration), then the blocks share out (section, chunk)
+// items, 64 chunks per section, one warp per row.
+constexpr int WR_MAX_SECTIONS = 1024;    // 4^5 sections at the deepest of 6 levels
+constexpr int WR_CHUNKS = 64;
+
 __global__ void __launch_bounds__(256) k_write_rows(LevelDev L, ScreenConst sc)
 {
-    const int sec = blockIdx.y;
-    if (sec >= L.nsec) return;
-    const SecState &st = L.st[sec];
-    const int old = st.rows_from;
-    if (old <= 0 || st.done) return;
-    const int mc = st.mc;
-    const int pend = ((max(old, mc) + 127) / 128) * 128;
-    const int wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    const int gw = blockIdx.x * nw + wid, ngw = gridDim.x * nw;
-    for (int pos = gw; pos < mc; pos += ngw) write_row_any(L, sec, L.slot_of_pos[L.poff[sec] + pos], pos, sc);
-    for (int pos = mc + blockIdx.x * blockDim.x + threadIdx.x; pos < pend; pos += gridDim.x * blockDim.x)
-        mark_pos_dead(L, sec, pos);
+    __shared__ int32_t list[WR_MAX_SECTIONS];
+    __shared__ int32_t wcnt[32];
+    __shared__ int32_t nlist;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (threadIdx.x == 0) nlist = 0;
+    __syncthreads();
+    for (int c = 0; c < L.nsec; c += blockDim.x) {
+        const int sec = c + threadIdx.x;
+        bool f = false;
+        if (sec < L.nsec) {
+            const SecState &st = L.st[sec];
+            f = st.rows_from > 0 && !st.done;
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, f);
+        if (lane == 0) wcnt[wid] = __popc(bal);
+        __syncthreads();
+        int off = 0, tot = 0;
+        for (int k = 0; k < nw; k++) { if (k < wid) off += wcnt[k]; tot += wcnt[k]; }
+        if (f) list[nlist + off + __popc(bal & ((1u << lane) - 1))] = sec;
+        __syncthreads();
+        if (threadIdx.x == 0) nlist += tot;
+        __syncthreads();
+    }
+    const int items = nlist * WR_CHUNKS;
+    for (int it = blockIdx.x; it < items; it += gridDim.x) {
+        const int sec = list[it / WR_CHUNKS], chunk = it % WR_CHUNKS;
+        const SecState &st = L.st[sec];
+        const int old = st.rows_from, mc = st.mc;
+        const int pend = ((max(old, mc) + 127) / 128) * 128;
+        const int gw = chunk * nw + wid, ngw = WR_CHUNKS * nw;
+        for (int pos = gw; pos < mc; pos += ngw) write_row_any(L, sec, L.slot_of_pos[L.poff[sec] + pos], pos, sc);
+        for (int pos = mc + chunk * blockDim.x + threadIdx.x; pos < pend; pos += WR_CHUNKS * blockDim.x)
+            mark_pos_dead(L, sec, pos);
+    }
 }
 
 // Units of this step's tensor-core screen that may hold a pair with K < t
