@@ -93,6 +93,22 @@ class ClockSampler:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
+def max_over_ranks(x: float, dist, device) -> float:
+    """Max of a per-rank scalar over all ranks (x itself when dist is None)."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(world: int, pairs_per_step: int, steps: int, seconds: float) -> float:
+    """Whole-job throughput of `world` replicas, each running `steps` steps of
+    `pairs_per_step` pairs: pairs of all ranks / the slowest rank's time."""
+    return world * pairs_per_step * steps / seconds
+
+
 def workload(k, rows=None, cols=None):
     import synth
     w = synth.WORKLOADS[k]
@@ -218,14 +234,11 @@ def main():
     e1.record(stream)
     torch.cuda.synchronize()
     clocks = clk.stop()
-    ms = e0.elapsed_time(e1)
+    ms = max_over_ranks(e0.elapsed_time(e1), dist, "cuda")
     if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
         dist.barrier()
     pairs = stats[-1]["pairs"]
-    value = world * pairs * args.steps / (ms / 1000.0)
+    value = job_rate(world, pairs, args.steps, ms / 1000.0)
 
     # dominant kernel: the spectral screen; algorithmic flops 2*B per screened pair
     peaks = load_peaks()
@@ -299,13 +312,9 @@ def main():
             lab, sums, cnt = segh.level(nl - 1)
             d2h = lab.nbytes + sums.nbytes + cnt.nbytes
         torch.cuda.synchronize()
-        te = time.perf_counter() - t0
-        if dist:
-            t = torch.tensor([te], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            te = float(t.item())
+        te = max_over_ranks(time.perf_counter() - t0, dist, "cuda")
         h2d = img.nbytes + (0 if mask is None else mask.nbytes)
-        line["e2e"] = {"value": world * pairs * args.steps / te, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+        line["e2e"] = {"value": job_rate(world, pairs, args.steps, te), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                        "d2h_bytes_per_step": int(d2h), "seconds_per_step": te / args.steps}
         segh.close()
 
