@@ -51,3 +51,15 @@ def test_gram_rejects_bad_shapes(P):
         P.gram_tc(torch.zeros(128, 40, dtype=torch.float16, device="cuda"))
     with pytest.raises(P.RHSEGError):
         P.gram_tc(torch.zeros(128, 48, dtype=torch.float16, device="cuda"))
+
+
+@pytest.mark.parametrize("precision", [1, 2])
+def test_screen_error_on_region_means_within_bound(P, precision):
+    """The screen arithmetic's error on real operands (the root-level regions
+    of the 145x145x200 run and 2048 random pixels of its cube), through the
+    tensor-core Gram, stays within the bound the reject test relies on."""
+    from paper_2106_12942_b300.studies import screen_error
+    for r in screen_error(precision=precision):
+        assert r["pairs"] > 1000, r
+        assert r["max_err_over_bound"] <= 1.0, r
+        print(r)
