@@ -183,6 +183,8 @@ def main():
     ap.add_argument("--precision", type=int, default=None)
     ap.add_argument("--incremental", type=int, default=None, choices=[0, 1],
                     help="1: incremental spectral minima (same results, row updates instead of the all-pairs screen)")
+    ap.add_argument("--multi-merge", type=int, default=None, choices=[0, 1],
+                    help="1: several merges per iteration (a different rule; its own oracle mode)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--rows", type=int, default=None, help="scaled-down image (profiling); not a bench line")
@@ -211,6 +213,8 @@ def main():
         params["precision"] = args.precision
     if args.incremental is not None:
         params["incremental"] = args.incremental
+    if args.multi_merge is not None:
+        params["multi_merge"] = args.multi_merge
     params["profile"] = 1
     stream = torch.cuda.current_stream()
     img_d = torch.from_numpy(img.view(np.int16)).cuda().view(torch.uint16)
@@ -275,7 +279,8 @@ def main():
         "data": "synthetic",
         "config": {"workload": w.name, "rows": w.rows, "cols": w.cols, "bands": w.bands,
                    "rnb_levels": params["rnb_levels"], "spclust_wght": params["spclust_wght"],
-                   "conv_nregions": params["conv_nregions"], "precision": prec, "parallelism": f"replicas{world}",
+                   "conv_nregions": params["conv_nregions"], "precision": prec,
+                   "multi_merge": params.get("multi_merge", 0), "parallelism": f"replicas{world}",
                    "l2": "inputs larger than L2 (cube 470 MB, region tables several GB)",
                    "pairs_per_step": pairs, "seconds_per_rhseg_run": ms / args.steps / 1000.0},
         "roofline": roofline,

@@ -85,6 +85,14 @@ typedef struct rhseg_params {
                               all pairs each iteration (results identical; needs the
                               binary32 rows, precision 3, else RHSEG_EINVAL).  The level-start pass and the row
                               updates are timed as the screen (stats screen_ms). */
+    int32_t multi_merge;   /* 1: several merges per HSEG iteration (Section 6.2 names the
+                              idea; reading R12): in each step every region takes its
+                              best partner, and all mutually best pairs merge, smallest
+                              key first, until the target.  The spectral threshold is
+                              (w*w) times the iteration's smallest adjacent key.  Results
+                              differ from the single-merge rule (0, default) and match
+                              the oracle's multi-merge mode.  Not with incremental = 1
+                              (RHSEG_EINVAL). */
 } rhseg_params;
 
 /* One merge-log record.  kind 0 = adjacent merge, 1 = spectral merge,

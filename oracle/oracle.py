@@ -42,6 +42,7 @@ class Params(C.Structure):
         ("seam_pass", C.c_int32),
         ("mode", C.c_int32),
         ("full_adjacency", C.c_int32),
+        ("multi_merge", C.c_int32),
     ]
 
 
@@ -161,6 +162,7 @@ def _params(**kw) -> Params:
     p.seam_pass = kw.get("seam_pass", 1)
     p.mode = kw.get("mode", 1)
     p.full_adjacency = kw.get("full_adjacency", 0)
+    p.multi_merge = kw.get("multi_merge", 0)
     return p
 
 

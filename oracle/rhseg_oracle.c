@@ -55,6 +55,16 @@
  *   R10 Pairs evaluated per iteration = number of adjacent pairs in the
  *       adjacent step + (if the spectral step runs) number of non-adjacent
  *       pairs in the spectral step.
+ *   R12 Multiple merges per iteration (Section 6.2 names the idea only;
+ *       params.multi_merge = 1).  In each stage every region takes its best
+ *       partner among the stage's pairs (R2 order): adjacent pairs in the
+ *       adjacent stage; non-adjacent pairs with K < t in the spectral stage.
+ *       The mutually best pairs are disjoint, so each keeps its key while the
+ *       others merge.  They merge in (K, lo ID, hi ID) order with the R4 stop
+ *       test after each.  t = (w*w) * K_adj, with K_adj the smallest key
+ *       merged in the adjacent stage (the global minimum, which is always
+ *       mutually best), on the state after that stage.  The first merge of
+ *       every iteration is therefore the single-merge rule's.
  */
 #include <stdint.h>
 #include <stdlib.h>
@@ -148,6 +158,7 @@ typedef struct {
     int32_t mode;            /* 0 plain: every key recomputed each iteration;
                                 1 cached: key matrix, touched row recomputed */
     int32_t full_adjacency;  /* test hook: every pair counts as adjacent */
+    int32_t multi_merge;     /* reading R12: all mutually best pairs per stage */
 } orc_params;
 
 typedef struct {
@@ -272,11 +283,88 @@ static void sect_merge(sect_t *s, int a, int b)
 typedef struct snapctl snapctl_t;
 static int take_snapshot(snapctl_t *c, const sect_t *s);
 
+typedef struct { int i, j; double K; int64_t lo, hi; } mpair_t;
+
+static int cmp_mpair(const void *a, const void *b)
+{
+    const mpair_t *x = (const mpair_t *)a, *y = (const mpair_t *)b;
+    if (pair_less(x->K, x->lo, x->hi, y->K, y->lo, y->hi)) return -1;
+    if (pair_less(y->K, y->lo, y->hi, x->K, x->lo, x->hi)) return 1;
+    return 0;
+}
+
+/*
+ * One stage of reading R12: spectral = 0 takes the adjacent pairs, 1 the
+ * non-adjacent pairs with K < t.  Each region's best partner, then the
+ * mutually best pairs merged in (K, lo, hi) order until the count reaches
+ * the target.  *nmerged = merges done, *kfirst = key of the first merge.
+ */
+static int stage_multi(sect_t *s, int spectral, double t, int mode, int *count, int target, int level,
+                       int section, int32_t iter, mlog_t *log, orc_stats *st, snapctl_t *snap,
+                       int *nmerged, double *kfirst)
+{
+    int m = s->m;
+    *nmerged = 0;
+    *kfirst = INFINITY;
+    if (m == 0) return ORC_OK;
+    int *best = (int *)malloc((size_t)m * sizeof(int));
+    double *bK = (double *)malloc((size_t)m * sizeof(double));
+    mpair_t *P = (mpair_t *)malloc((size_t)(m / 2 + 1) * sizeof(mpair_t));
+    if (!best || !bK || !P) { free(best); free(bK); free(P); return ORC_ENOMEM; }
+    for (int i = 0; i < m; i++) { best[i] = -1; bK[i] = INFINITY; }
+    int64_t npairs = 0;
+    for (int i = 0; i < m; i++) {
+        if (!s->alive[i]) continue;
+        for (int j = i + 1; j < m; j++) {
+            if (!s->alive[j]) continue;
+            int a = s->adj[(size_t)i * m + j] != 0;
+            if (a == spectral) continue;
+            npairs++;
+            double K = (mode == 1) ? s->kmat[(size_t)i * m + j] : sect_key(s, i, j);
+            if (spectral && !(K < t)) continue;
+            /* slots are in ID order: the pair is (id[i], id[j]) */
+            if (best[i] < 0 || pair_less(K, s->id[i], s->id[j], bK[i],
+                                         s->id[i] < s->id[best[i]] ? s->id[i] : s->id[best[i]],
+                                         s->id[i] < s->id[best[i]] ? s->id[best[i]] : s->id[i])) {
+                best[i] = j; bK[i] = K;
+            }
+            if (best[j] < 0 || pair_less(K, s->id[i], s->id[j], bK[j],
+                                         s->id[j] < s->id[best[j]] ? s->id[j] : s->id[best[j]],
+                                         s->id[j] < s->id[best[j]] ? s->id[best[j]] : s->id[j])) {
+                best[j] = i; bK[j] = K;
+            }
+        }
+    }
+    st->pairs += npairs;
+    int np = 0;
+    for (int i = 0; i < m; i++) {
+        int j = best[i];
+        if (j > i && best[j] == i) {
+            mpair_t q = { i, j, bK[i], s->id[i], s->id[j] };
+            P[np++] = q;
+        }
+    }
+    qsort(P, (size_t)np, sizeof(mpair_t), cmp_mpair);
+    int rc = ORC_OK;
+    for (int k = 0; k < np && *count > target; k++) {
+        sect_merge(s, P[k].i, P[k].j);
+        (*count)--;
+        if (*nmerged == 0) *kfirst = P[k].K;
+        (*nmerged)++;
+        if (spectral) st->merges_spec++; else st->merges_adj++;
+        orc_merge rec = { level, section, iter, spectral, P[k].lo, P[k].hi, P[k].K, sqrt(P[k].K), *count, 0 };
+        if ((rc = log_push(log, rec))) break;
+        if (snap && (rc = take_snapshot(snap, s))) break;
+    }
+    free(best); free(bK); free(P);
+    return rc;
+}
+
 /*
  * HSEG on one section (steps 2-4 of Section 4.1 with readings R2-R4, R10).
  * Returns ORC_OK; *stalled set when an iteration merged nothing.
  */
-static int hseg(sect_t *s, int target, double w, int mode, int level, int section,
+static int hseg(sect_t *s, int target, double w, int mode, int multi, int level, int section,
                 mlog_t *log, orc_stats *st, int64_t max_iters, snapctl_t *snap, int *stalled)
 {
     int m = s->m;
@@ -297,6 +385,21 @@ static int hseg(sect_t *s, int target, double w, int mode, int level, int sectio
         if (max_iters > 0 && st->iterations >= max_iters) break;
         iter++;
         st->iterations++;
+        if (multi) {
+            /* reading R12: both stages merge every mutually best pair */
+            int na = 0, ns = 0;
+            double ka = INFINITY, ks = INFINITY;
+            int rc = stage_multi(s, 0, INFINITY, mode, &count, target, level, section, iter, log, st, snap, &na, &ka);
+            if (rc) return rc;
+            if (count <= target) break;
+            if (w > 0.0) {
+                double t = na ? (w * w) * ka : INFINITY;
+                rc = stage_multi(s, 1, t, mode, &count, target, level, section, iter, log, st, snap, &ns, &ks);
+                if (rc) return rc;
+            }
+            if (na + ns == 0) { *stalled = 1; break; }
+            continue;
+        }
         /* --- step 2: adjacent pairs --- */
         int bi = -1, bj = -1;
         double bK = INFINITY;
@@ -720,6 +823,7 @@ void *orc_run(const uint16_t *img, int32_t rows, int32_t cols, int32_t bands,
         p->rnb_levels > 12 || !(p->spclust_wght >= 0.0 && p->spclust_wght <= 1.0) ||
         p->conv_nregions < 1 || (p->connectivity != 4 && p->connectivity != 8) ||
         p->min_nregions < 0 || p->n_out_levels < 0 || (p->mode != 0 && p->mode != 1) ||
+        (p->multi_merge != 0 && p->multi_merge != 1) ||
         (int64_t)rows * cols >= ((int64_t)1 << 31) - 1) {
         *err = ORC_EINVAL;
         return NULL;
@@ -804,7 +908,7 @@ void *orc_run(const uint16_t *img, int32_t rows, int32_t cols, int32_t bands,
             rlist_free(&regs);
             int target = (lev == 1) ? p->conv_nregions : min_nr;
             int stalled = 0;
-            rc = hseg(&sec, target, p->spclust_wght, p->mode, lev, (int32_t)s, &R->log, &R->st, 0, scp, &stalled);
+            rc = hseg(&sec, target, p->spclust_wght, p->mode, p->multi_merge, lev, (int32_t)s, &R->log, &R->st, 0, scp, &stalled);
             if (stalled) R->st.stalled_sections++;
             if (rc == ORC_OK && scp) {
                 /* levels never reached (stall) take the final state */
@@ -892,6 +996,7 @@ int32_t orc_hseg_leaf(const uint16_t *img, int32_t rows, int32_t cols, int32_t b
 {
     if (!img || rows <= 0 || cols <= 0 || bands <= 0 || !p || p->rnb_levels < 1 ||
         (p->connectivity != 4 && p->connectivity != 8) || (p->mode != 0 && p->mode != 1) ||
+        (p->multi_merge != 0 && p->multi_merge != 1) ||
         section < 0 || section >= ((int64_t)1 << (2 * (p->rnb_levels - 1))))
         return ORC_EINVAL;
     orc_run_t *R = (orc_run_t *)calloc(1, sizeof(orc_run_t));
@@ -926,7 +1031,7 @@ int32_t orc_hseg_leaf(const uint16_t *img, int32_t rows, int32_t cols, int32_t b
     if (rc == ORC_OK) {
         int target = (L == 1) ? p->conv_nregions : (p->min_nregions > 0 ? p->min_nregions : p->conv_nregions);
         int stalled = 0;
-        rc = hseg(&sec, target, p->spclust_wght, p->mode, L, (int32_t)section, &R->log, &R->st,
+        rc = hseg(&sec, target, p->spclust_wght, p->mode, p->multi_merge, L, (int32_t)section, &R->log, &R->st,
                   max_iters, NULL, &stalled);
         if (stalled) R->st.stalled_sections++;
         sect_free(&sec);

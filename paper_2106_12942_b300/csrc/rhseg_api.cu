@@ -156,6 +156,10 @@ struct rhseg_handle {
     DBuf<int32_t> ulist;
     DBuf<unsigned long long> sortk;
     DBuf<IncInfo> sinfo;
+    // several merges per iteration
+    DBuf<unsigned long long> mlist;
+    DBuf<uint64_t> mK;
+    DBuf<uint32_t> mP;
     // per level, sized at run time
     DBuf<uint32_t> adj;
     DBuf<int64_t> aoff;
@@ -197,6 +201,8 @@ static int check_params(const rhseg_params *p, int32_t rows, int32_t cols, int32
     if (p->precision < 0 || p->precision > 3 || p->profile < 0 || p->profile > 1) return RHSEG_EINVAL;
     if (p->incremental < 0 || p->incremental > 1) return RHSEG_EINVAL;
     if (p->incremental && p->precision != 3) return RHSEG_EINVAL;   // binary32 rows only
+    if (p->multi_merge < 0 || p->multi_merge > 1) return RHSEG_EINVAL;
+    if (p->multi_merge && p->incremental) return RHSEG_EINVAL;
     return RHSEG_OK;
 }
 
@@ -443,6 +449,11 @@ static int common_create(rhseg_handle *h, const rhseg_params *p, void *stream)
         if ((rc = h->srowx.alloc((size_t)h->geo[p->rnb_levels].nsec * h->Bpad * INC_RCAP))) return rc;
         if ((rc = h->sinfo.alloc((size_t)h->geo[p->rnb_levels].nsec))) return rc;
         CK(cudaMemset(h->inR.p, 0, P));
+    }
+    if (p->multi_merge) {
+        if ((rc = h->mlist.alloc(2 * P))) return rc;
+        if ((rc = h->mK.alloc(P))) return rc;
+        if ((rc = h->mP.alloc(P))) return rc;
     }
     if (screen_uses_tcgen05(p->precision)) {
         int mr = make_operand_map(&h->tmap, h->X.p, (int64_t)h->npos, h->Bpad, p->precision);
@@ -827,6 +838,10 @@ static int run_impl(rhseg_handle *h)
         if (skip_units) {
             D.nlo = h->nlo.p; D.nhi = h->nhi.p; D.sk = h->sk.p;
             D.ulist = h->ulist.p; D.ucap = ucap; D.sortk = h->sortk.p;
+        }
+        if (h->p.multi_merge) {
+            D.multi = 1;
+            D.mlist = h->mlist.p; D.mK = h->mK.p; D.mP = h->mP.p;
         }
         if (inc) {
             D.H = nullptr;
@@ -1236,6 +1251,7 @@ extern "C" void rhseg_destroy(rhseg_handle *h)
     h->ckey.release(); h->inR.release(); h->sT.release(); h->sE.release(); h->sk.release(); h->sbuf.release();
     h->nlo.release(); h->nhi.release(); h->ulist.release();
     h->sortk.release();
+    h->mlist.release(); h->mK.release(); h->mP.release();
     h->srowx.release(); h->sinfo.release();
     h->slot_of_pos.release(); h->X.release(); h->Af.release(); h->kf.release(); h->H.release(); h->Ad.release(); h->kd.release();
     h->adj.release(); h->aoff.release(); h->Wrow.release(); h->ref.release(); h->cand.release(); h->st.release();

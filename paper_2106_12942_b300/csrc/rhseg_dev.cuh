@@ -102,6 +102,11 @@ struct LevelDev {
     float *srowx;              // per section: staged row vectors of a row update [Bpad][8]
     struct IncInfo *sinfo;     // per section: state of a row update between its kernels
     unsigned long long *ckey;  // [nsec][cand_cap] exact keys of candidates
+    // several merges per iteration (reading R12; null unless that mode is on)
+    int32_t multi;
+    unsigned long long *mlist; // per slot x 2: the stage's mutually best pairs (K bits, (i << 32) | j)
+    uint64_t *mK;              // per slot: K bits of the best below-threshold non-adjacent pair
+    uint32_t *mP;              // per slot: partner slot of that pair (~0u: none)
 };
 
 // ---------------------------------------------------------------------------

@@ -751,6 +751,74 @@ __device__ void block_merge(const LevelDev &L, int sec, SecState &st, int a, int
     __syncthreads();
 }
 
+// ---------------------------------------------------------------------------
+// Several merges per iteration (reading R12; Section 6.2 names the idea).
+// ---------------------------------------------------------------------------
+
+// Every live slot i whose best partner j > i has i as its own best partner
+// gives one pair; such pairs are disjoint.  They are listed in the
+// section's scratch as (K bits, (i << 32) | j) and sorted ascending: slots are
+// in ID order, so this is the (K, lo ID, hi ID) order.  Then they merge one
+// by one in that order while the count is above the target; each keeps its
+// listed key, since the other listed pairs do not touch its two regions.
+// bK / bP: the stage's per-slot best (bP < 0 or bK = RHSEG_KEY_NONE: none).
+// Returns the merges done (uniform over the block); *kfirst = the first
+// one's key, the stage's smallest.
+__device__ int block_merge_mutual(const LevelDev &L, int sec, SecState &st, const uint64_t *bK,
+                                  const int32_t *bP, int kind, const ScreenConst &sc, StepSmem &sm,
+                                  double *kfirst)
+{
+    const int64_t ro = L.roff[sec];
+    const int m0 = st.m0;
+    unsigned long long *list = L.mlist + 2 * ro;       // 2 m0 words: n <= m0 / 2 pairs, padded n2 <= m0
+    __shared__ int32_t nmut;
+    if (threadIdx.x == 0) nmut = 0;
+    __syncthreads();
+    for (int i = threadIdx.x; i < m0; i += blockDim.x) {
+        const unsigned long long k = __ldcg((const unsigned long long *)bK + ro + i);
+        const int32_t j = __ldcg(bP + ro + i);
+        if (k == RHSEG_KEY_NONE || j <= i || j >= m0) continue;
+        if (__ldcg(bP + ro + j) != i) continue;
+        const int e = atomicAdd(&nmut, 1);
+        list[2 * e] = k;
+        list[2 * e + 1] = ((unsigned long long)(uint32_t)i << 32) | (uint32_t)j;
+    }
+    __syncthreads();
+    const int n = nmut;
+    int n2 = n > 0 ? 1 : 0;
+    while (n2 < n) n2 <<= 1;
+    for (int e = n + threadIdx.x; e < n2; e += blockDim.x) { list[2 * e] = ~0ull; list[2 * e + 1] = ~0ull; }
+    __syncthreads();
+    // bitonic sort of the n2 entries on (K bits, slot pair)
+    for (int k = 2; k <= n2; k <<= 1)
+        for (int d = k >> 1; d > 0; d >>= 1) {
+            for (int i = threadIdx.x; i < n2; i += blockDim.x) {
+                const int l = i ^ d;
+                if (l <= i) continue;
+                const unsigned long long ak = list[2 * i], at = list[2 * i + 1];
+                const unsigned long long bk = list[2 * l], bt = list[2 * l + 1];
+                const bool gt = ak > bk || (ak == bk && at > bt);
+                if (gt == ((i & k) == 0)) {
+                    list[2 * i] = bk; list[2 * i + 1] = bt;
+                    list[2 * l] = ak; list[2 * l + 1] = at;
+                }
+            }
+            __syncthreads();
+        }
+    int done = 0;
+    *kfirst = __longlong_as_double(0x7FF0000000000000ll);
+    for (int e = 0; e < n; e++) {
+        if (st.count <= st.target) break;              // st.count is updated inside block_merge
+        const unsigned long long kb = list[2 * e], t = list[2 * e + 1];
+        const double K = __longlong_as_double((long long)kb);
+        if (e == 0) *kfirst = K;
+        block_merge(L, sec, st, (int)(t >> 32), (int)(t & 0xffffffffu), K, kind, sc, sm);
+        done++;
+    }
+    __syncthreads();
+    return done;
+}
+
 // New position list of the live slots in order of their rows' certified
 // norms (the tensor-core screen then finds whole units of pairs far apart in
 // norm, which its norm bound proves to be above the threshold).  Bitonic
@@ -1047,20 +1115,28 @@ __global__ void __launch_bounds__(STEP_THREADS, 2) k_adj_step(LevelDev L, Screen
     const int m0 = st.m0;
     __syncthreads();
     if (threadIdx.x == 0) { st.iter += 1; st.pairs += st.nadj; st.rows_from = 0; }
+    __syncthreads();
     PairKey best = pk_none();
-    for (int i = threadIdx.x; i < m0; i += blockDim.x) {
-        // absorbed slots carry RHSEG_KEY_NONE
-        const uint64_t k = L.bestK[ro + i];
-        const int32_t bp = L.bestP[ro + i];
-        if (k == RHSEG_KEY_NONE) continue;
-        const PairKey c = pk_make(k, i, bp);
-        if (pk_less(c, best)) best = c;
+    if (!L.multi) {
+        for (int i = threadIdx.x; i < m0; i += blockDim.x) {
+            // absorbed slots carry RHSEG_KEY_NONE
+            const uint64_t k = L.bestK[ro + i];
+            const int32_t bp = L.bestP[ro + i];
+            if (k == RHSEG_KEY_NONE) continue;
+            const PairKey c = pk_make(k, i, bp);
+            if (pk_less(c, best)) best = c;
+        }
+        best = block_min_pk(best, sm.pk);
     }
-    best = block_min_pk(best, sm.pk);
     __syncthreads();
     int merged = 0;
     double Kadj = __longlong_as_double(0x7FF0000000000000ll);
-    if (best.k != RHSEG_KEY_NONE) {
+    if (L.multi) {
+        // reading R12: every mutually best adjacent pair; the threshold of the
+        // spectral stage comes from the first (smallest) of them
+        double k0;
+        if (block_merge_mutual(L, sec, st, L.bestK, L.bestP, 0, sc, sm, &k0) > 0) { merged = 1; Kadj = k0; }
+    } else if (best.k != RHSEG_KEY_NONE) {
         Kadj = __longlong_as_double((long long)best.k);
         block_merge(L, sec, st, (int)best.lo, (int)best.hi, Kadj, 0, sc, sm);
         merged = 1;
@@ -1129,48 +1205,81 @@ __global__ void __launch_bounds__(STEP_THREADS, 2) k_spec_step(LevelDev L, Scree
     const uint64_t tbits = dbits(t);
     PairKey best = pk_none();
     long long ntrue = 0;
-    if (!exhaustive) {
-        const uint32_t *cand = L.cand + (int64_t)sec * L.cand_cap * 2;
-        const int32_t *sop = L.slot_of_pos + L.poff[sec];
-        for (uint32_t c0 = 0; c0 < ncand; c0 += PAIR_CAP) {
-            __syncthreads();
-            if (tid == 0) sm.npair = 0;
-            __syncthreads();
-            for (uint32_t c = c0 + tid; c < min(ncand, c0 + PAIR_CAP); c += nt) {
-                const int i = sop[cand[2 * c]], j = sop[cand[2 * c + 1]];
-                if (i == j || !L.alive[ro + i] || !L.alive[ro + j]) continue;
-                if ((A[(int64_t)i * W + (j >> 5)] >> (j & 31)) & 1) continue;
-                const int idx = atomicAdd(&sm.npair, 1);
-                sm.pi[idx] = min(i, j);
-                sm.pj[idx] = max(i, j);
+    // reading R12: pass 0 takes every slot's smallest below-threshold key,
+    // pass 1 the smallest partner among the pairs with that key (for a fixed
+    // slot, the (K, lo, hi) order of its pairs is the order of the partner)
+    if (L.multi) {
+        for (int i = tid; i < m0; i += nt) { L.mK[ro + i] = RHSEG_KEY_NONE; L.mP[ro + i] = ~0u; }
+        __syncthreads();
+    }
+    const int npass = L.multi ? 2 : 1;
+    for (int pass = 0; pass < npass; pass++) {
+        if (!exhaustive) {
+            const uint32_t *cand = L.cand + (int64_t)sec * L.cand_cap * 2;
+            const int32_t *sop = L.slot_of_pos + L.poff[sec];
+            for (uint32_t c0 = 0; c0 < ncand; c0 += PAIR_CAP) {
+                __syncthreads();
+                if (tid == 0) sm.npair = 0;
+                __syncthreads();
+                for (uint32_t c = c0 + tid; c < min(ncand, c0 + PAIR_CAP); c += nt) {
+                    const int i = sop[cand[2 * c]], j = sop[cand[2 * c + 1]];
+                    if (i == j || !L.alive[ro + i] || !L.alive[ro + j]) continue;
+                    if ((A[(int64_t)i * W + (j >> 5)] >> (j & 31)) & 1) continue;
+                    const int idx = atomicAdd(&sm.npair, 1);
+                    sm.pi[idx] = min(i, j);
+                    sm.pj[idx] = max(i, j);
+                }
+                __syncthreads();
+                const int np = sm.npair;
+                block_keys(L, ro, sm.pi, sm.pj, sm.pkey, np);
+                __syncthreads();
+                for (int e = tid; e < np; e += nt) {
+                    const uint64_t kb = sm.pkey[e];
+                    if (!(kb < tbits)) continue;          // K < t (both non-negative binary64)
+                    const int i = sm.pi[e], j = sm.pj[e];
+                    if (!L.multi) {
+                        ntrue++;
+                        const PairKey pc = pk_make(kb, i, j);
+                        if (pk_less(pc, best)) best = pc;
+                    } else if (pass == 0) {
+                        ntrue++;
+                        atomicMin((unsigned long long *)L.mK + ro + i, (unsigned long long)kb);
+                        atomicMin((unsigned long long *)L.mK + ro + j, (unsigned long long)kb);
+                    } else {
+                        if (kb == __ldcg((const unsigned long long *)L.mK + ro + i)) atomicMin(L.mP + ro + i, (uint32_t)j);
+                        if (kb == __ldcg((const unsigned long long *)L.mK + ro + j)) atomicMin(L.mP + ro + j, (uint32_t)i);
+                    }
+                }
             }
-            __syncthreads();
-            const int np = sm.npair;
-            block_keys(L, ro, sm.pi, sm.pj, sm.pkey, np);
-            __syncthreads();
-            for (int e = tid; e < np; e += nt) {
-                const uint64_t kb = sm.pkey[e];
-                if (!(kb < tbits)) continue;          // K < t (both non-negative binary64)
-                ntrue++;
-                const PairKey pc = pk_make(kb, sm.pi[e], sm.pj[e]);
-                if (pk_less(pc, best)) best = pc;
+        } else {
+            // every unordered pair of live, non-adjacent slots
+            const int lane = tid & 31;
+            const int64_t npair = (int64_t)m0 * (m0 - 1) / 2;
+            for (int64_t e = wid; e < npair; e += nw) {
+                int64_t i = (int64_t)((2.0 * m0 - 1 - sqrt((2.0 * m0 - 1) * (2.0 * m0 - 1) - 8.0 * e)) / 2);
+                while (i > 0 && i * (2 * m0 - i - 1) / 2 > e) i--;
+                while ((i + 1) * (2 * m0 - i - 2) / 2 <= e) i++;
+                const int64_t j = e - i * (2 * m0 - i - 1) / 2 + i + 1;
+                if (!L.alive[ro + i] || !L.alive[ro + j]) continue;
+                if ((A[i * W + (j >> 5)] >> (j & 31)) & 1) continue;
+                const double K = warp_key(L.S + (ro + i) * L.Bs, L.n[ro + i], L.S + (ro + j) * L.Bs, L.n[ro + j], L.B, L.err);
+                if (!(K < t)) continue;
+                const uint64_t kb = dbits(K);
+                if (!L.multi) {
+                    const PairKey pc = pk_make(kb, (int)i, (int)j);
+                    if (pk_less(pc, best)) best = pc;
+                } else if (lane == 0) {
+                    if (pass == 0) {
+                        atomicMin((unsigned long long *)L.mK + ro + i, (unsigned long long)kb);
+                        atomicMin((unsigned long long *)L.mK + ro + j, (unsigned long long)kb);
+                    } else {
+                        if (kb == __ldcg((const unsigned long long *)L.mK + ro + i)) atomicMin(L.mP + ro + i, (uint32_t)j);
+                        if (kb == __ldcg((const unsigned long long *)L.mK + ro + j)) atomicMin(L.mP + ro + j, (uint32_t)i);
+                    }
+                }
             }
         }
-    } else {
-        // every unordered pair of live, non-adjacent slots
-        const int64_t npair = (int64_t)m0 * (m0 - 1) / 2;
-        for (int64_t e = wid; e < npair; e += nw) {
-            int64_t i = (int64_t)((2.0 * m0 - 1 - sqrt((2.0 * m0 - 1) * (2.0 * m0 - 1) - 8.0 * e)) / 2);
-            while (i > 0 && i * (2 * m0 - i - 1) / 2 > e) i--;
-            while ((i + 1) * (2 * m0 - i - 2) / 2 <= e) i++;
-            const int64_t j = e - i * (2 * m0 - i - 1) / 2 + i + 1;
-            if (!L.alive[ro + i] || !L.alive[ro + j]) continue;
-            if ((A[i * W + (j >> 5)] >> (j & 31)) & 1) continue;
-            const double K = warp_key(L.S + (ro + i) * L.Bs, L.n[ro + i], L.S + (ro + j) * L.Bs, L.n[ro + j], L.B, L.err);
-            if (!(K < t)) continue;
-            const PairKey pc = pk_make(dbits(K), (int)i, (int)j);
-            if (pk_less(pc, best)) best = pc;
-        }
+        __syncthreads();
     }
     ntrue = block_sum_ll(ntrue, sm.ll);
     best = block_min_pk(best, sm.pk);
@@ -1183,7 +1292,10 @@ __global__ void __launch_bounds__(STEP_THREADS, 2) k_spec_step(LevelDev L, Scree
         if (!exhaustive) st.screened += (int64_t)mc * (mc - 1) / 2;
     }
     int merged = 0;
-    if (best.k != RHSEG_KEY_NONE) {
+    if (L.multi) {
+        double k0;
+        merged = block_merge_mutual(L, sec, st, L.mK, (const int32_t *)L.mP, 1, sc, sm, &k0) > 0;
+    } else if (best.k != RHSEG_KEY_NONE) {
         block_merge(L, sec, st, (int)best.lo, (int)best.hi, __longlong_as_double((long long)best.k), 1, sc, sm);
         merged = 1;
     }

@@ -18,7 +18,8 @@ import numpy as np
 from . import _abi
 
 DEFAULTS = dict(rnb_levels=1, conv_nregions=1, spclust_wght=0.0, connectivity=8, min_nregions=0,
-                n_out_levels=1, seam_pass=1, precision=1, profile=0, incremental=0)
+                n_out_levels=1, seam_pass=1, precision=1, profile=0, incremental=0,
+                multi_merge=0)
 
 
 class RHSEGError(RuntimeError):

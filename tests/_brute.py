@@ -56,7 +56,7 @@ def section_rect(rows, cols, lev, s):
 
 class Brute:
     def __init__(self, img, mask, rnb_levels=1, spclust_wght=0.0, conv_nregions=1, connectivity=8,
-                 min_nregions=0, n_out_levels=1, seam_pass=1):
+                 min_nregions=0, n_out_levels=1, seam_pass=1, multi_merge=0):
         self.rows, self.cols, self.B = img.shape
         self.pix = {}
         for r in range(self.rows):
@@ -68,6 +68,7 @@ class Brute:
         self.min_nr = min_nregions or conv_nregions
         self.n_out = n_out_levels or 1
         self.seam = seam_pass
+        self.multi = multi_merge
         self.log = []
         self.pairs = 0
         self.levels = []
@@ -97,10 +98,62 @@ class Brute:
                         adj.add((min(rid, o), max(rid, o)))
         return adj
 
+    def _mutual_stage(self, regs, cands, target, lev, sec, it, kind, snaps):
+        """Reading R12: cands maps each pair (a, b), a < b, to (K, a, b).
+        Every region's best candidate; the pairs that are best for both
+        ends, merged smallest first while above the target."""
+        best = {}
+        for (a, b), k in cands.items():
+            for r in (a, b):
+                if r not in best or k < best[r]:
+                    best[r] = k
+        mutual = sorted({k for k in best.values() if best[k[1]] == k and best[k[2]] == k})
+        done = []
+        for K, a, b in mutual:
+            if len(regs) <= target:
+                break
+            regs[a] = regs[a] | regs.pop(b)
+            done.append(K)
+            self.log.append((lev, sec, it, kind, a, b, K, len(regs)))
+            if snaps is not None:
+                snaps(regs)
+        return done
+
+    def _hseg_multi(self, regs, rect, target, lev, sec, snaps):
+        it = 0
+        while len(regs) > target:
+            it += 1
+            adj = self.adjacent(regs, rect)
+            self.pairs += len(adj)
+            cands = {(a, b): (rkey(self.pix, regs[a], regs[b]), a, b) for (a, b) in adj}
+            done_a = self._mutual_stage(regs, cands, target, lev, sec, it, 0, snaps)
+            if len(regs) <= target:
+                break
+            done_s = []
+            if self.w > 0:
+                t = (self.w * self.w) * min(done_a) if done_a else float("inf")
+                adj = self.adjacent(regs, rect)
+                ids = sorted(regs)
+                cands = {}
+                for i, a in enumerate(ids):
+                    for b in ids[i + 1:]:
+                        if (a, b) in adj:
+                            continue
+                        self.pairs += 1
+                        K = rkey(self.pix, regs[a], regs[b])
+                        if K < t:
+                            cands[(a, b)] = (K, a, b)
+                done_s = self._mutual_stage(regs, cands, target, lev, sec, it, 1, snaps)
+            if not done_a and not done_s:
+                break
+        return regs
+
     def hseg(self, regs, rect, target, lev, sec, snaps=None):
         it = 0
         if snaps is not None:
             snaps(regs)
+        if self.multi:
+            return self._hseg_multi(regs, rect, target, lev, sec, snaps)
         while len(regs) > target:
             it += 1
             adj = self.adjacent(regs, rect)

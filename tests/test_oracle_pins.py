@@ -237,7 +237,16 @@ MUTANTS = [
     ("ties rounded away from zero", "up = (int)(mant & 1);", "up = 1;"),
     ("Z order of children", "else if (digit == 1) { r.r1 = r.r0 + h2; r.c0 = r.c0 + w2; }\n        else if (digit == 2) { r.r0 = r.r0 + h2; r.c1 = r.c0 + w2; }",
      "else if (digit == 2) { r.r1 = r.r0 + h2; r.c0 = r.c0 + w2; }\n        else if (digit == 1) { r.r0 = r.r0 + h2; r.c1 = r.c0 + w2; }"),
+    ("multi-merge: pairs merged without the mutual test", "if (j > i && best[j] == i) {", "if (j > i) {"),
+    ("multi-merge: stage merged in slot order, not key order", "qsort(P, (size_t)np, sizeof(mpair_t), cmp_mpair);",
+     "(void)cmp_mpair;"),
+    ("multi-merge: no stop test inside a stage", "for (int k = 0; k < np && *count > target; k++)",
+     "for (int k = 0; k < np; k++)"),
+    ("multi-merge: threshold from the last adjacent merge", "if (*nmerged == 0) *kfirst = P[k].K;",
+     "*kfirst = P[k].K;"),
 ]
+
+MULTI_CASES = [1, 3, 4, 5, 7, 9, 10, 12]          # indices into BRUTE_CASES
 
 
 def _pins_pass(orc, L):
@@ -261,19 +270,49 @@ def _pins_pass(orc, L):
                                                 for a, b in zip(Si, Sj))
         if orc.key(ni, Si, nj, Sj, L=L) != float(want):
             return False
-    for case in BRUTE_CASES:
+    for ci, case in enumerate(BRUTE_CASES):
         rows, cols, B, maxval, mask_p, Lv, w, conv, conn, min_nr, n_out, seam = case
         img, mask = synth.random_cube(101 + rows * 7 + cols, rows, cols, B, maxval, mask_p)
         kw = dict(rnb_levels=Lv, spclust_wght=w, conv_nregions=conv, connectivity=conn,
                   min_nregions=min_nr, n_out_levels=n_out, seam_pass=seam)
-        br = _brute.Brute(img, mask, **kw).run()
-        r = orc.run(img, mask, L=L, mode=0, **kw)
-        if _log_tuples(r.log) != br.log:
-            return False
-        for lv, (lab, _, _) in zip(r.levels, br.levels):
-            if lv.labels.tolist() != lab:
+        for multi in ((0, 1) if ci in MULTI_CASES else (0,)):
+            br = _brute.Brute(img, mask, multi_merge=multi, **kw).run()
+            r = orc.run(img, mask, L=L, mode=0, multi_merge=multi, **kw)
+            if _log_tuples(r.log) != br.log:
                 return False
+            for lv, (lab, _, _) in zip(r.levels, br.levels):
+                if lv.labels.tolist() != lab:
+                    return False
+    d, img = _multi_fixture()
+    for case in d["cases"]:
+        r = orc.run(img, None, L=L, mode=0, **_case_params(d, case))
+        if _fixture_log(r.log) != _fixture_want(case) or r.stats["pairs"] != case["pairs"]:
+            return False
     return True
+
+
+def _multi_fixture():
+    import json
+    d = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "worked_1x6_multi_merge.json")))
+    im = d["image"]
+    return d, np.array(im["values"], dtype=np.uint16).reshape(im["rows"], im["cols"], im["bands"])
+
+
+def _case_params(d, case):
+    kw = dict(d["params"], spclust_wght=case["spclust_wght"])
+    if "conv_nregions" in case:
+        kw["conv_nregions"] = case["conv_nregions"]
+    return kw
+
+
+def _fixture_log(log):
+    return [(int(m["step"]), int(m["kind"]), int(m["survivor_id"]), int(m["absorbed_id"]), float(m["key"]))
+            for m in log]
+
+
+def _fixture_want(case):
+    from fractions import Fraction
+    return [(st, k, a, b, float(Fraction(K))) for st, k, a, b, K in case["log"]]
 
 
 def test_unmodified_oracle_passes_compact_pins(orc):
@@ -292,3 +331,111 @@ def test_planted_mistake_is_caught(orc, tmp_path, what, orig, bad):
     so = orc.compile_source(str(path), str(tmp_path / "mutant.so"))
     L = orc.load(so)
     assert not _pins_pass(orc, L), what
+
+
+# --- reading R12: several merges per iteration (params multi_merge = 1) ---
+
+def test_multi_merge_worked_example_fixture(orc):
+    d, img = _multi_fixture()
+    for case in d["cases"]:
+        want = _fixture_want(case)
+        kw = _case_params(d, case)
+        for mode in (0, 1):
+            r = orc.run(img, None, mode=mode, **kw)
+            assert _fixture_log(r.log) == want, (case["spclust_wght"], mode)
+            assert r.stats["pairs"] == case["pairs"]
+        br = _brute.Brute(img, None, **kw).run()
+        assert [(it, k, a, b, K) for (_, _, it, k, a, b, K, _) in br.log] == want
+        assert br.pairs == case["pairs"]
+
+
+@pytest.mark.parametrize("ci", MULTI_CASES)
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_multi_merge_oracle_equals_brute_force(orc, ci, seed):
+    rows, cols, B, maxval, mask_p, L, w, conv, conn, min_nr, n_out, seam = BRUTE_CASES[ci]
+    img, mask = synth.random_cube(seed * 101 + rows * 7 + cols, rows, cols, B, maxval, mask_p)
+    kw = dict(rnb_levels=L, spclust_wght=w, conv_nregions=conv, connectivity=conn,
+              min_nregions=min_nr, n_out_levels=n_out, seam_pass=seam, multi_merge=1)
+    br = _brute.Brute(img, mask, **kw).run()
+    for mode in (0, 1):
+        r = orc.run(img, mask, mode=mode, **kw)
+        assert _log_tuples(r.log) == br.log
+        assert r.stats["pairs"] == br.pairs
+        for lv, (lab, sums, counts) in zip(r.levels, br.levels):
+            assert lv.labels.tolist() == lab
+            assert lv.counts.tolist() == counts
+            assert lv.sums.tolist() == sums
+
+
+def _stage_groups(log):
+    """Records grouped by (level, section, step, kind), in log order."""
+    groups, key = [], None
+    for m in log:
+        k = (int(m["level"]), int(m["section"]), int(m["step"]), int(m["kind"]))
+        if k != key:
+            groups.append([])
+            key = k
+        groups[-1].append(m)
+    return groups
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_multi_merge_invariants_piecewise(orc, seed):
+    """Properties of the rule at sizes the brute force cannot reach: within a
+    stage the merged pairs are disjoint and come in (K, lo, hi) order; the
+    count drops by one per record; the first merge of a section equals the
+    single-merge rule's first merge; spectral merges stay below the
+    iteration's threshold; sums and counts are conserved; and the rule needs
+    no more iterations than the single-merge rule."""
+    rows, cols, L, w = [(24, 24, 2, 0.5), (21, 27, 2, 0.2), (32, 32, 3, 1.0)][seed]
+    img, mask = synth.make(2, seed=300 + seed, rows=rows, cols=cols)
+    img = np.ascontiguousarray(img[:, :, :6])
+    kw = dict(rnb_levels=L, spclust_wght=w, conv_nregions=6, connectivity=8, n_out_levels=3)
+    multi = orc.run(img, mask, multi_merge=1, **kw)
+    single = orc.run(img, mask, multi_merge=0, **kw)
+    assert orc.run(img, mask, multi_merge=1, mode=0, **kw).log.tobytes() == multi.log.tobytes()
+    groups = _stage_groups(multi.log[multi.log["kind"] != 2])
+    assert any(len(g) > 1 for g in groups)
+    for g in groups:
+        ids = [int(m["survivor_id"]) for m in g] + [int(m["absorbed_id"]) for m in g]
+        assert len(set(ids)) == len(ids)
+        keys = [(float(m["key"]), int(m["survivor_id"]), int(m["absorbed_id"])) for m in g]
+        assert keys == sorted(keys)
+        assert all(int(m["survivor_id"]) < int(m["absorbed_id"]) for m in g)
+    prev = None
+    for m in multi.log:
+        if prev is not None and (m["level"], m["section"]) == (prev["level"], prev["section"]) and m["kind"] != 2 \
+                and prev["kind"] != 2:
+            assert int(m["nregions_after"]) == int(prev["nregions_after"]) - 1
+        prev = m
+    thr = {}
+    for g in groups:
+        m0 = g[0]
+        k = (int(m0["level"]), int(m0["section"]), int(m0["step"]))
+        if int(m0["kind"]) == 0:
+            thr[k] = (w * w) * float(m0["key"])
+        else:
+            assert all(float(m["key"]) < thr.get(k, float("inf")) for m in g)
+    deepest = L
+    for s in range(4 ** (L - 1)):
+        a = multi.log[(multi.log["level"] == deepest) & (multi.log["section"] == s)]
+        b = single.log[(single.log["level"] == deepest) & (single.log["section"] == s)]
+        if len(b):
+            assert a[0].tobytes() == b[0].tobytes()
+    assert multi.stats["iterations"] <= single.stats["iterations"]
+    tot = img.reshape(-1, img.shape[2]).astype(np.int64)
+    keep = (mask == 0).ravel() if mask is not None else np.ones(tot.shape[0], bool)
+    for lv in multi.levels:
+        assert np.array_equal(lv.sums.sum(axis=0), tot[keep].sum(axis=0))
+        assert lv.counts.sum() == keep.sum()
+
+
+def test_multi_merge_one_merge_equals_single_merge(orc):
+    """With a target one below the start count the rule makes exactly the
+    single-merge rule's merge."""
+    img, mask = synth.random_cube(77, 6, 7, 3, 50, 0.0)
+    for w in (0.0, 0.5, 1.0):
+        kw = dict(rnb_levels=1, spclust_wght=w, conv_nregions=6 * 7 - 1, connectivity=8)
+        a = orc.run(img, mask, multi_merge=1, **kw)
+        b = orc.run(img, mask, multi_merge=0, **kw)
+        assert a.log.tobytes() == b.log.tobytes() and len(a.log) == 1
