@@ -439,3 +439,39 @@ def test_multi_merge_one_merge_equals_single_merge(orc):
         a = orc.run(img, mask, multi_merge=1, **kw)
         b = orc.run(img, mask, multi_merge=0, **kw)
         assert a.log.tobytes() == b.log.tobytes() and len(a.log) == 1
+
+
+def test_multi_merge_complete_adjacency_gives_the_ward_dendrogram(orc):
+    """Ward linkage is reducible (Lance-Williams), so merging every pair of
+    reciprocal nearest neighbours at once, and repeating, builds the same
+    dendrogram as the sequential algorithm (the basis of the
+    nearest-neighbour-chain method).  With every pair adjacent and w = 0 the
+    several-merges rule is exactly that: its clusters and heights must be
+    scipy's Ward linkage, in a different order, in fewer iterations."""
+    from scipy.cluster.hierarchy import linkage
+    rng = np.random.default_rng(23)
+    fewer = 0
+    for trial in range(8):
+        n, B = int(rng.integers(6, 48)), int(rng.integers(1, 5))
+        X = rng.integers(0, 65536, (n, B)).astype(np.uint16)
+        img = X.reshape(1, n, B)
+        r = orc.run(img, None, rnb_levels=1, spclust_wght=0.0, conv_nregions=1, full_adjacency=1, multi_merge=1)
+        Z = linkage(X.astype(np.float64), method="ward")
+        assert len(r.log) == n - 1
+        members = {i: {i} for i in range(n)}
+        scip = {}
+        for k, (a, b, h, _) in enumerate(Z):
+            s = members.pop(int(a)) | members.pop(int(b))
+            members[n + k] = s
+            scip[frozenset(s)] = h
+        groups = {i + 1: {i} for i in range(n)}
+        ours = {}
+        for m in r.log:
+            s = groups[int(m["survivor_id"])] | groups.pop(int(m["absorbed_id"]))
+            groups[int(m["survivor_id"])] = s
+            ours[frozenset(s)] = np.sqrt(2 * float(m["key"]))
+        assert set(ours) == set(scip)
+        for c, h in scip.items():
+            assert abs(ours[c] - h) <= 1e-9 * h
+        fewer += r.stats["iterations"] < n - 1
+    assert fewer > 0
