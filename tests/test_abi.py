@@ -75,6 +75,30 @@ int main(void) {
     assert b == [C.sizeof(_abi.Stats), _abi.Stats.stalled_sections.offset, _abi.Stats.run_ms.offset]
 
 
+def test_every_field_offset_matches_header(so_path):
+    # every field of the three structures, by name, against offsetof() in C
+    from paper_2106_12942_b300 import _abi
+    structs = [("rhseg_params", _abi.Params), ("rhseg_merge", _abi.Merge), ("rhseg_stats", _abi.Stats)]
+    lines = []
+    want = []
+    for cname, py in structs:
+        lines.append(f'  printf("%zu\\n", sizeof({cname}));')
+        want.append(C.sizeof(py))
+        for f, _ in py._fields_:
+            lines.append(f'  printf("%zu\\n", offsetof({cname}, {f}));')
+            want.append(getattr(py, f).offset)
+    src = "#include <stdio.h>\n#include <stddef.h>\n#include \"rhseg.h\"\nint main(void) {\n" + \
+          "\n".join(lines) + "\n  return 0;\n}\n"
+    import tempfile
+    with tempfile.TemporaryDirectory() as d:
+        c = os.path.join(d, "t.c")
+        open(c, "w").write(src)
+        exe = os.path.join(d, "t")
+        subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), "-o", exe, c])
+        got = list(map(int, subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split()))
+    assert got == want
+
+
 def test_strerror_is_host_only(so_path):
     from paper_2106_12942_b300 import _abi
     L = _abi.load(so_path)
@@ -89,6 +113,7 @@ def test_param_validation_needs_no_device(so_path):
     h = C.c_void_p()
     img = (C.c_uint16 * 4)()
     for bad in [dict(spclust_wght=1.5), dict(connectivity=6), dict(rnb_levels=0), dict(rnb_levels=7),
-                dict(precision=9), dict(conv_nregions=0)]:
+                dict(precision=9), dict(conv_nregions=0), dict(incremental=1, precision=1),
+                dict(multi_merge=2), dict(multi_merge=1, incremental=1, precision=3)]:
         p = make_params(**bad)
         assert L.rhseg_create(img, 2, 2, 1, None, C.byref(p), None, C.byref(h)) == _abi.RHSEG_EINVAL
