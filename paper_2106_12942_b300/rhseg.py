@@ -8,6 +8,15 @@
 `image` is uint16 [rows, cols, bands]; a numpy array goes through
 rhseg_create (host buffers, copied to the device), a CUDA torch tensor
 through rhseg_create_device (stays owned by the caller).
+
+Keyword parameters mirror rhseg_params of include/rhseg.h (defaults in
+DEFAULTS): rnb_levels, conv_nregions, spclust_wght, connectivity,
+min_nregions, n_out_levels, seam_pass; precision (screen arithmetic, same
+merges in every form: 1 FP16 tensor cores, 2 BF16 tensor cores, 3 FP32, 0
+FP64); incremental (1: exact per-region spectral minima, precision 3 only,
+same merges); multi_merge (1: all mutually best pairs per stage merge in one
+iteration, a different rule with its own oracle mode); profile (1: per-kernel
+CUDA-event times in stats()).
 """
 from __future__ import annotations
 
