@@ -3,13 +3,17 @@
 // Data layout of a level (all sections of the level at once):
 //   slots      regions present at the level start, section-local index sorted
 //              by region ID (so slot order = ID order, reading R5);
-//   positions  compact list of live slots used by the spectral screen,
-//              rebuilt (stable) once an eighth of them died;
+//   positions  compact list of live slots used by the spectral screen
+//              (tensor-core forms: in certified-norm order), rebuilt with
+//              the order kept whenever the live count drops below a
+//              128-position block boundary;
 //   adjacency  one dense bitmap per section, m0 x W words (W = ceil(m0/32)
 //              rounded to 4), symmetric, no self bits;
 //   bestK/P    per slot: the smallest (K, pair) over its adjacent partners
 //              (kept exact and current after every merge);
-//   log        one segment per (level, section).
+//   log        one segment per (level, section);
+//   mlist      (multi_merge only) per slot x 2 words: a stage's mutually best
+//              pairs, sorted, before they merge.
 #pragma once
 #include "rhseg_dev.cuh"
 #include "../../include/rhseg.h"
