@@ -69,6 +69,24 @@ def test_plain_equals_cached_on_piecewise_scenes(orc):
             assert np.array_equal(x.labels, y.labels) and np.array_equal(x.sums, y.sums)
 
 
+def test_plain_equals_cached_on_workloads(orc):
+    # the 32x32x16 workload in full under both merge rules, and the first
+    # iterations of a 145x145x200 section (plain mode recomputes every pair)
+    img, mask = synth.make(1)
+    kw = {k: v for k, v in synth.WORKLOADS[1].params.items() if k != "precision"}
+    for multi in (0, 1):
+        a = orc.run(img, mask, mode=0, multi_merge=multi, **kw)
+        b = orc.run(img, mask, mode=1, multi_merge=multi, **kw)
+        assert np.array_equal(a.log, b.log) and a.stats == b.stats
+        assert np.array_equal(a.levels[-1].labels, b.levels[-1].labels)
+    img, mask = synth.make(2)
+    kw = {k: v for k, v in synth.WORKLOADS[2].params.items() if k != "precision"}
+    for multi in (0, 1):
+        a = orc.hseg_leaf(img, mask, 5, max_iters=10 if multi == 0 else 2, mode=0, multi_merge=multi, **kw)
+        b = orc.hseg_leaf(img, mask, 5, max_iters=10 if multi == 0 else 2, mode=1, multi_merge=multi, **kw)
+        assert len(a.log) >= 10 and np.array_equal(a.log, b.log)
+
+
 def test_complete_adjacency_is_unconstrained_ward(orc):
     # Every pair adjacent, w = 0, one level: HSEG is Ward's agglomeration;
     # scipy's Ward heights are sqrt(2 K) (K = increase of the within-cluster
