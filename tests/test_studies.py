@@ -101,3 +101,15 @@ def test_screen_error_bound_catches_a_perturbed_gram():
     assert screen_error_of(S, n, 1, bad)["max_err_over_bound"] > 1.0
     drop = lambda Xh: _f32_gram(Xh[:, :-40].contiguous())             # a band block left out
     assert screen_error_of(S, n, 1, drop)["max_err_over_bound"] > 1.0
+
+
+def test_screen_rows_scale_keeps_fp16_finite():
+    torch = pytest.importorskip("torch")
+    from paper_2106_12942_b300.studies import screen_rows
+    n = np.array([1, 3, 7, 1], np.int64)
+    S = np.stack([np.full(5, 65535) * n[0], np.zeros(5, np.int64), np.full(5, 65535) * n[2], np.full(5, 17)])
+    x32, s, xs = screen_rows(S, n, 32)
+    assert np.abs(x32).max() < 2.0 ** 15 and s >= 1
+    assert torch.isfinite(torch.from_numpy(x32).half()).all()
+    assert np.allclose(x32[:, :5], xs, rtol=2.0 ** -22, atol=0)
+    assert np.all(x32[:, 5:] == 0)
