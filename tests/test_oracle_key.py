@@ -79,6 +79,30 @@ def test_key_matches_exact_rational_over_means(orc):
         assert orc.key(ni, Si, nj, Sj) == float(_K_means(ni, Si, nj, Sj))
 
 
+def test_key_at_the_edge_of_the_exact_range(orc):
+    # largest counts, band counts and value spreads the exact-key bound
+    # N < 2^127 admits (D = n_i n_j (n_i + n_j) then far above 2^64)
+    rng = np.random.default_rng(17)
+    cases = [(1 << 21, 1 << 21, 224), (1 << 21, (1 << 21) + 12345, 224), (1, 1 << 40, 4), (3, 1 << 38, 16),
+             ((1 << 22) - 1, 1 << 19, 200), (1 << 16, 1 << 16, 4096)]
+    done = 0
+    for ni, nj, B in cases:
+        for _ in range(4):
+            mi = rng.integers(0, 65536, B)
+            mj = rng.integers(0, 65536, B)
+            mi[0], mj[0] = 65535, 0                                   # one band at the full spread
+            Si = [int(v) * ni + int(rng.integers(0, ni)) for v in mi]
+            Sj = [int(v) * nj + int(rng.integers(0, nj)) for v in mj]
+            N = sum((nj * a - ni * b) ** 2 for a, b in zip(Si, Sj))
+            if N >= 2**127 or max(max(Si), max(Sj)) >= 2**63:
+                continue
+            want = Fraction(N, ni * nj * (ni + nj))
+            assert want == _K_means(ni, Si, nj, Sj)
+            assert orc.key(ni, np.array(Si, np.int64), nj, np.array(Sj, np.int64)) == float(want), (ni, nj, B)
+            done += 1
+    assert done >= 16
+
+
 def test_key_is_symmetric_and_zero_on_equal_means(orc):
     rng = np.random.default_rng(9)
     for _ in range(100):
