@@ -493,3 +493,26 @@ def test_multi_merge_complete_adjacency_gives_the_ward_dendrogram(orc):
             assert abs(ours[c] - h) <= 1e-9 * h
         fewer += r.stats["iterations"] < n - 1
     assert fewer > 0
+
+
+def test_oracle_equals_brute_force_random_sweep(orc):
+    """Random configurations beyond the fixed list: sizes up to 7x7, 1-3
+    bands, value ranges small enough for ties, L up to 3, every weight class,
+    both connectivities, seam pass on and off, masks, both merge rules."""
+    rng = np.random.default_rng(2024)
+    for k in range(300):
+        rows, cols = int(rng.integers(1, 8)), int(rng.integers(2, 8))
+        B, maxval = int(rng.integers(1, 4)), int(rng.choice([2, 4, 9, 40]))
+        mask_p = float(rng.choice([0.0, 0.0, 0.15]))
+        L = int(rng.integers(1, 4 if min(rows, cols) >= 4 else 3)) if min(rows, cols) >= 2 else 1
+        kw = dict(rnb_levels=L, spclust_wght=float(rng.choice([0.0, 0.3, 0.5, 1.0])),
+                  conv_nregions=int(rng.integers(1, 4)), connectivity=int(rng.choice([4, 8])),
+                  min_nregions=int(rng.integers(0, 4)), n_out_levels=int(rng.integers(1, 4)),
+                  seam_pass=int(rng.integers(0, 2)), multi_merge=int(rng.integers(0, 2)))
+        img, mask = synth.random_cube(5000 + k, rows, cols, B, maxval, mask_p)
+        br = _brute.Brute(img, mask, **kw).run()
+        r = orc.run(img, mask, mode=int(k % 2), **kw)
+        assert _log_tuples(r.log) == br.log, (k, kw)
+        assert r.stats["pairs"] == br.pairs, (k, kw)
+        for lv, (lab, sums, counts) in zip(r.levels, br.levels):
+            assert lv.labels.tolist() == lab and lv.counts.tolist() == counts and lv.sums.tolist() == sums, (k, kw)
