@@ -76,7 +76,7 @@ def compile_source(src: str, so: str) -> str:
     by the mutation tests, which compile edited copies)."""
     tmp = so + f".{os.getpid()}.tmp"
     subprocess.check_call(
-        ["gcc", "-O2", "-std=gnu11", "-fno-fast-math", "-ffp-contract=off", "-shared", "-fPIC",
+        ["gcc", "-O2", "-std=gnu11", "-fno-fast-math", "-ffp-contract=off", "-shared", "-fPIC", "-pthread",
          "-o", tmp, src, "-lm"])
     os.replace(tmp, so)
     return so
@@ -92,6 +92,9 @@ def load(so_path: str):
     L.orc_run.restype = C.c_void_p
     L.orc_run.argtypes = [C.c_void_p, C.c_int32, C.c_int32, C.c_int32, C.c_void_p,
                           C.POINTER(Params), C.POINTER(C.c_int32)]
+    L.orc_run_threads.restype = C.c_void_p
+    L.orc_run_threads.argtypes = [C.c_void_p, C.c_int32, C.c_int32, C.c_int32, C.c_void_p,
+                                  C.POINTER(Params), C.c_int32, C.POINTER(C.c_int32)]
     L.orc_log_len.restype = C.c_int64
     L.orc_log_len.argtypes = [C.c_void_p]
     L.orc_get_log.restype = None
@@ -176,18 +179,24 @@ class OracleError(RuntimeError):
         self.code = code
 
 
-def run(image: np.ndarray, mask: np.ndarray | None = None, L=None, **kw) -> Result:
+def run(image: np.ndarray, mask: np.ndarray | None = None, L=None, threads: int = 1, **kw) -> Result:
     """Full RHSEG run.  image: uint16 [rows, cols, bands]; mask: [rows, cols]
     nonzero = no data.  Keyword parameters as in Params (mode 1 = cached keys,
-    0 = every key recomputed each iteration)."""
+    0 = every key recomputed each iteration).  threads > 1 runs the
+    independent sections of each level on that many threads; the result is
+    the same for every thread count."""
     img = np.ascontiguousarray(image, dtype=np.uint16)
     rows, cols, bands = img.shape
     mk = None if mask is None else np.ascontiguousarray(mask, dtype=np.uint8)
     p = _params(**kw)
     err = C.c_int32(0)
     L = L or lib()
-    h = L.orc_run(img.ctypes.data, rows, cols, bands, None if mk is None else mk.ctypes.data,
-                  C.byref(p), C.byref(err))
+    if threads == 1:
+        h = L.orc_run(img.ctypes.data, rows, cols, bands, None if mk is None else mk.ctypes.data,
+                      C.byref(p), C.byref(err))
+    else:
+        h = L.orc_run_threads(img.ctypes.data, rows, cols, bands, None if mk is None else mk.ctypes.data,
+                              C.byref(p), int(threads), C.byref(err))
     if not h:
         raise OracleError(err.value)
     try:

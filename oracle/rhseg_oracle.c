@@ -1,5 +1,11 @@
 /*
- * rhseg_oracle.c -- plain, slow, single-threaded reference of RHSEG/HSEG.
+ * rhseg_oracle.c -- plain, slow reference of RHSEG/HSEG.
+ *
+ * Every section's HSEG runs in one thread.  The sections of one recursion
+ * level are independent (Section 4.1: a section only meets its siblings when
+ * the four are reassembled one level up), so orc_run_threads may run them on
+ * several threads and then joins their records in Z order; orc_run uses one.
+ * The thread count changes no result (a pin checks it).
  *
  * TEST INFRASTRUCTURE ONLY.  Nothing in the library links, includes or calls
  * this file; only tests/, the smoke check in __graft_entry__ and the CPU
@@ -70,6 +76,7 @@
 #include <stdlib.h>
 #include <string.h>
 #include <math.h>
+#include <pthread.h>
 
 typedef unsigned __int128 u128;
 typedef __int128 i128;
@@ -652,7 +659,8 @@ static int collect_survivors(orc_run_t *R, const rect_t *rc, sect_t *s, rlist_t 
 
 /* Seam pass (reading R7) on parent rectangle `pr` whose regions are `regs`
  * (sorted by ID, labels current).  Modifies regs and labels in place. */
-static int seam_pass(orc_run_t *R, const rect_t *pr, int lev, int64_t sec, rlist_t *regs)
+static int seam_pass(orc_run_t *R, const rect_t *pr, int lev, int64_t sec, rlist_t *regs, mlog_t *log,
+                     orc_stats *st)
 {
     int B = R->B, cols = R->cols;
     int h2 = (pr->r1 - pr->r0) / 2, w2 = (pr->c1 - pr->c0) / 2;
@@ -759,9 +767,9 @@ static int seam_pass(orc_run_t *R, const rect_t *pr, int lev, int64_t sec, rlist
             int p = y * cols + x;
             orc_merge m = { lev, (int32_t)sec, 0, 2, old_id[rs], (int64_t)p + 1,
                             split_key[li], sqrt(split_key[li]), regs->n, 0 };
-            rc = log_push(&R->log, m);
+            rc = log_push(log, m);
             if (rc) break;
-            R->st.seam_splits++;
+            st->seam_splits++;
         }
     free(split_of); free(split_key); free(xp); free(old_id); free(newid);
     return rc;
@@ -812,18 +820,130 @@ static int range_ok(int64_t P, int64_t maxval, int B)
 }
 
 /*
- * Full RHSEG run.  img is [rows][cols][bands] uint16, mask [rows][cols]
- * (nonzero = no data) or NULL.  Returns a handle or NULL with *err set.
+ * One section of one level (Section 4.1): its regions (the pixels at the
+ * deepest level; else the survivors of its four children, then the seam
+ * pass), HSEG to the section's target, the survivors into cur[s].  The
+ * section writes only the label-map pixels of its own rectangle and the
+ * slot_of_id entries of its own region IDs (an ID is a raster index of one
+ * of its pixels), and its records and counters go to its own log and stats;
+ * so the sections of one level are independent, as the recursion makes them.
  */
-void *orc_run(const uint16_t *img, int32_t rows, int32_t cols, int32_t bands,
-              const uint8_t *mask, const orc_params *p, int32_t *err)
+static int run_section(orc_run_t *R, int lev, int64_t s, rlist_t *prev, rlist_t *cur, mlog_t *log, orc_stats *st)
+{
+    const orc_params *p = &R->p;
+    int rows = R->rows, cols = R->cols, bands = R->B;
+    int64_t P = (int64_t)rows * cols;
+    int L = p->rnb_levels;
+    int min_nr = p->min_nregions > 0 ? p->min_nregions : p->conv_nregions;
+    rect_t rc_ = section_rect(rows, cols, lev, s);
+    rlist_t regs = { NULL, 0 };
+    int rc = ORC_OK;
+    if (lev == L) {
+        int area = (rc_.r1 - rc_.r0) * (rc_.c1 - rc_.c0);
+        regs.v = (oreg_t *)calloc((size_t)(area ? area : 1), sizeof(oreg_t));
+        if (!regs.v) return ORC_ENOMEM;
+        for (int y = rc_.r0; y < rc_.r1 && rc == ORC_OK; y++)
+            for (int x = rc_.c0; x < rc_.c1; x++) {
+                int q = y * cols + x;
+                if (!pix_unmasked(R, q)) continue;
+                oreg_t r;
+                r.id = (int64_t)q + 1; r.n = 1;
+                r.S = (int64_t *)malloc((size_t)bands * sizeof(int64_t));
+                if (!r.S) { rc = ORC_ENOMEM; break; }
+                for (int b = 0; b < bands; b++) r.S[b] = R->img[(size_t)q * bands + b];
+                regs.v[regs.n++] = r;
+            }
+        if (rc) { rlist_free(&regs); return rc; }
+    } else {
+        int tot = 0;
+        for (int c = 0; c < 4; c++) tot += prev[4 * s + c].n;
+        regs.v = (oreg_t *)calloc((size_t)(tot ? tot : 1), sizeof(oreg_t));
+        if (!regs.v) return ORC_ENOMEM;
+        for (int c = 0; c < 4; c++) {
+            rlist_t *ch = &prev[4 * s + c];
+            for (int i = 0; i < ch->n; i++) regs.v[regs.n++] = ch->v[i];
+            free(ch->v); ch->v = NULL; ch->n = 0;   /* ownership moved */
+        }
+        qsort(regs.v, (size_t)regs.n, sizeof(oreg_t), cmp_oreg);
+        if (p->seam_pass) {
+            rc = seam_pass(R, &rc_, lev, s, &regs, log, st);
+            if (rc) { rlist_free(&regs); return rc; }
+        }
+    }
+    sect_t sec;
+    rc = build_section(R, &rc_, &regs, &sec);
+    if (rc) { rlist_free(&regs); return rc; }
+    snapctl_t sc, *scp = NULL;
+    int32_t *pix_slot = NULL;
+    if (lev == 1) {
+        rc = make_targets(R, (int64_t)regs.n);
+        if (rc) { sect_free(&sec); rlist_free(&regs); return rc; }
+        pix_slot = (int32_t *)malloc((size_t)P * sizeof(int32_t));
+        if (!pix_slot) { sect_free(&sec); rlist_free(&regs); return ORC_ENOMEM; }
+        for (int64_t q = 0; q < P; q++)
+            pix_slot[q] = R->label[q] ? R->slot_of_id[R->label[q]] : -1;
+        sc.run = R; sc.rect = rc_; sc.pix_slot = pix_slot; sc.next = 0;
+        scp = &sc;
+    }
+    rlist_free(&regs);
+    int target = (lev == 1) ? p->conv_nregions : min_nr;
+    int stalled = 0;
+    rc = hseg(&sec, target, p->spclust_wght, p->mode, p->multi_merge, lev, (int32_t)s, log, st, 0, scp, &stalled);
+    if (stalled) st->stalled_sections++;
+    if (rc == ORC_OK && scp) {
+        /* levels never reached (stall) take the final state */
+        while (sc.next < R->nlev) {
+            R->targets[sc.next] = 0;
+            for (int i = 0; i < sec.m; i++) R->targets[sc.next] += sec.alive[i];
+            rc = take_snapshot(&sc, &sec);
+            if (rc) break;
+        }
+    }
+    free(pix_slot);
+    if (rc == ORC_OK) rc = collect_survivors(R, &rc_, &sec, &cur[s]);
+    sect_free(&sec);
+    return rc;
+}
+
+/* The sections of one level, shared out to worker threads one at a time. */
+typedef struct {
+    orc_run_t *R;
+    int lev;
+    int64_t nsec;
+    rlist_t *prev, *cur;
+    mlog_t *logs;            /* [nsec] */
+    orc_stats *sts;          /* [nsec] */
+    int *rcs;                /* [nsec] */
+    int64_t next;            /* next section to take (atomic) */
+} level_job_t;
+
+static void *level_worker(void *arg)
+{
+    level_job_t *J = (level_job_t *)arg;
+    for (;;) {
+        int64_t s = __atomic_fetch_add(&J->next, 1, __ATOMIC_RELAXED);
+        if (s >= J->nsec) break;
+        J->rcs[s] = run_section(J->R, J->lev, s, J->prev, J->cur, &J->logs[s], &J->sts[s]);
+    }
+    return NULL;
+}
+
+/*
+ * Full RHSEG run.  img is [rows][cols][bands] uint16, mask [rows][cols]
+ * (nonzero = no data) or NULL.  The sections of a level run on `nthreads`
+ * threads (1 = all in the calling thread); their records are then joined in
+ * Z order, so the log, the levels and the counters do not depend on
+ * nthreads.  Returns a handle or NULL with *err set.
+ */
+void *orc_run_threads(const uint16_t *img, int32_t rows, int32_t cols, int32_t bands,
+                      const uint8_t *mask, const orc_params *p, int32_t nthreads, int32_t *err)
 {
     *err = ORC_OK;
     if (!img || rows <= 0 || cols <= 0 || bands <= 0 || !p || p->rnb_levels < 1 ||
         p->rnb_levels > 12 || !(p->spclust_wght >= 0.0 && p->spclust_wght <= 1.0) ||
         p->conv_nregions < 1 || (p->connectivity != 4 && p->connectivity != 8) ||
         p->min_nregions < 0 || p->n_out_levels < 0 || (p->mode != 0 && p->mode != 1) ||
-        (p->multi_merge != 0 && p->multi_merge != 1) ||
+        (p->multi_merge != 0 && p->multi_merge != 1) || nthreads < 1 || nthreads > 1024 ||
         (int64_t)rows * cols >= ((int64_t)1 << 31) - 1) {
         *err = ORC_EINVAL;
         return NULL;
@@ -847,94 +967,64 @@ void *orc_run(const uint16_t *img, int32_t rows, int32_t cols, int32_t bands,
     for (int64_t q = 0; q < P; q++) R->label[q] = (mask && mask[q]) ? 0 : (int32_t)(q + 1);
 
     int L = p->rnb_levels;
-    int min_nr = p->min_nregions > 0 ? p->min_nregions : p->conv_nregions;
-    int64_t nsec_deep = (int64_t)1 << (2 * (L - 1));
     rlist_t *prev = NULL;    /* survivors of the level below, by section */
     int rc = ORC_OK;
     for (int lev = L; lev >= 1 && rc == ORC_OK; lev--) {
         int64_t nsec = (int64_t)1 << (2 * (lev - 1));
         rlist_t *cur = (rlist_t *)calloc((size_t)nsec, sizeof(rlist_t));
-        if (!cur) { rc = ORC_ENOMEM; break; }
-        for (int64_t s = 0; s < nsec && rc == ORC_OK; s++) {
-            rect_t rc_ = section_rect(rows, cols, lev, s);
-            rlist_t regs = { NULL, 0 };
-            if (lev == L) {
-                int area = (rc_.r1 - rc_.r0) * (rc_.c1 - rc_.c0);
-                regs.v = (oreg_t *)calloc((size_t)(area ? area : 1), sizeof(oreg_t));
-                if (!regs.v) { rc = ORC_ENOMEM; break; }
-                for (int y = rc_.r0; y < rc_.r1; y++)
-                    for (int x = rc_.c0; x < rc_.c1; x++) {
-                        int q = y * cols + x;
-                        if (!pix_unmasked(R, q)) continue;
-                        oreg_t r;
-                        r.id = (int64_t)q + 1; r.n = 1;
-                        r.S = (int64_t *)malloc((size_t)bands * sizeof(int64_t));
-                        if (!r.S) { rc = ORC_ENOMEM; break; }
-                        for (int b = 0; b < bands; b++) r.S[b] = img[(size_t)q * bands + b];
-                        regs.v[regs.n++] = r;
-                    }
-                if (rc) { rlist_free(&regs); break; }
-            } else {
-                int tot = 0;
-                for (int c = 0; c < 4; c++) tot += prev[4 * s + c].n;
-                regs.v = (oreg_t *)calloc((size_t)(tot ? tot : 1), sizeof(oreg_t));
-                if (!regs.v) { rc = ORC_ENOMEM; break; }
-                for (int c = 0; c < 4; c++) {
-                    rlist_t *ch = &prev[4 * s + c];
-                    for (int i = 0; i < ch->n; i++) regs.v[regs.n++] = ch->v[i];
-                    free(ch->v); ch->v = NULL; ch->n = 0;   /* ownership moved */
-                }
-                qsort(regs.v, (size_t)regs.n, sizeof(oreg_t), cmp_oreg);
-                if (p->seam_pass) {
-                    rc = seam_pass(R, &rc_, lev, s, &regs);
-                    if (rc) { rlist_free(&regs); break; }
-                }
-            }
-            sect_t sec;
-            rc = build_section(R, &rc_, &regs, &sec);
-            if (rc) { rlist_free(&regs); break; }
-            snapctl_t sc, *scp = NULL;
-            int32_t *pix_slot = NULL;
-            if (lev == 1) {
-                rc = make_targets(R, (int64_t)regs.n);
-                if (rc) { sect_free(&sec); rlist_free(&regs); break; }
-                pix_slot = (int32_t *)malloc((size_t)P * sizeof(int32_t));
-                if (!pix_slot) { rc = ORC_ENOMEM; sect_free(&sec); rlist_free(&regs); break; }
-                for (int64_t q = 0; q < P; q++)
-                    pix_slot[q] = R->label[q] ? R->slot_of_id[R->label[q]] : -1;
-                sc.run = R; sc.rect = rc_; sc.pix_slot = pix_slot; sc.next = 0;
-                scp = &sc;
-            }
-            rlist_free(&regs);
-            int target = (lev == 1) ? p->conv_nregions : min_nr;
-            int stalled = 0;
-            rc = hseg(&sec, target, p->spclust_wght, p->mode, p->multi_merge, lev, (int32_t)s, &R->log, &R->st, 0, scp, &stalled);
-            if (stalled) R->st.stalled_sections++;
-            if (rc == ORC_OK && scp) {
-                /* levels never reached (stall) take the final state */
-                while (sc.next < R->nlev) {
-                    R->targets[sc.next] = 0;
-                    for (int i = 0; i < sec.m; i++) R->targets[sc.next] += sec.alive[i];
-                    rc = take_snapshot(&sc, &sec);
-                    if (rc) break;
-                }
-            }
-            free(pix_slot);
-            if (rc == ORC_OK) rc = collect_survivors(R, &rc_, &sec, &cur[s]);
-            sect_free(&sec);
+        mlog_t *logs = (mlog_t *)calloc((size_t)nsec, sizeof(mlog_t));
+        orc_stats *sts = (orc_stats *)calloc((size_t)nsec, sizeof(orc_stats));
+        int *rcs = (int *)calloc((size_t)nsec, sizeof(int));
+        if (!cur || !logs || !sts || !rcs) {
+            free(cur); free(logs); free(sts); free(rcs);
+            rc = ORC_ENOMEM;
+            break;
         }
+        level_job_t J = { R, lev, nsec, prev, cur, logs, sts, rcs, 0 };
+        int nt = nthreads < nsec ? nthreads : (int)nsec;
+        if (nt <= 1) {
+            level_worker(&J);
+        } else {
+            pthread_t *tid = (pthread_t *)calloc((size_t)nt, sizeof(pthread_t));
+            int started = 0;
+            if (tid)
+                for (; started < nt; started++)
+                    if (pthread_create(&tid[started], NULL, level_worker, &J) != 0) break;
+            if (started == 0) level_worker(&J);      /* no thread could start: run here */
+            for (int t = 0; t < started; t++) pthread_join(tid[t], NULL);
+            free(tid);
+        }
+        /* records and counters joined in Z order of the sections */
+        for (int64_t s = 0; s < nsec; s++) {
+            if (rcs[s] && rc == ORC_OK) rc = rcs[s];
+            for (int64_t k = 0; k < logs[s].n && rc == ORC_OK; k++) rc = log_push(&R->log, logs[s].v[k]);
+            R->st.pairs += sts[s].pairs;
+            R->st.iterations += sts[s].iterations;
+            R->st.merges_adj += sts[s].merges_adj;
+            R->st.merges_spec += sts[s].merges_spec;
+            R->st.seam_splits += sts[s].seam_splits;
+            R->st.stalled_sections += sts[s].stalled_sections;
+            free(logs[s].v);
+        }
+        free(logs); free(sts); free(rcs);
         if (prev) {
             int64_t pn = nsec * 4;
             for (int64_t s = 0; s < pn; s++) rlist_free(&prev[s]);
             free(prev);
         }
         prev = cur;
-        (void)nsec_deep;
     }
     if (prev) { rlist_free(&prev[0]); free(prev); }
     R->st.n_levels_out = R->nlev;
     if (rc) { orc_free(R); *err = rc; return NULL; }
     return R;
+}
+
+/* Full RHSEG run in the calling thread (see orc_run_threads). */
+void *orc_run(const uint16_t *img, int32_t rows, int32_t cols, int32_t bands,
+              const uint8_t *mask, const orc_params *p, int32_t *err)
+{
+    return orc_run_threads(img, rows, cols, bands, mask, p, 1, err);
 }
 
 int64_t orc_log_len(void *h) { return ((orc_run_t *)h)->log.n; }

@@ -516,3 +516,58 @@ def test_oracle_equals_brute_force_random_sweep(orc):
         assert r.stats["pairs"] == br.pairs, (k, kw)
         for lv, (lab, sums, counts) in zip(r.levels, br.levels):
             assert lv.labels.tolist() == lab and lv.counts.tolist() == counts and lv.sums.tolist() == sums, (k, kw)
+
+
+# --- the threaded driver over the sections of a level (full-size goldens) ---
+
+def _same_result(a, b):
+    if not np.array_equal(a.log, b.log) or a.stats != b.stats or len(a.levels) != len(b.levels):
+        return False
+    return all(np.array_equal(x.labels, y.labels) and np.array_equal(x.sums, y.sums)
+               and np.array_equal(x.counts, y.counts) for x, y in zip(a.levels, b.levels))
+
+
+@pytest.mark.parametrize("threads", [2, 3, 8])
+def test_threaded_run_equals_single_thread_on_tiny_cases(orc, threads):
+    # the brute-force cases with several sections per level, both merge rules
+    for ci, case in enumerate(BRUTE_CASES):
+        rows, cols, B, maxval, mask_p, L, w, conv, conn, min_nr, n_out, seam = case
+        if L < 2:
+            continue
+        img, mask = synth.random_cube(101 + rows * 7 + cols, rows, cols, B, maxval, mask_p)
+        kw = dict(rnb_levels=L, spclust_wght=w, conv_nregions=conv, connectivity=conn,
+                  min_nregions=min_nr, n_out_levels=n_out, seam_pass=seam)
+        for multi in (0, 1):
+            a = orc.run(img, mask, multi_merge=multi, **kw)
+            b = orc.run(img, mask, threads=threads, multi_merge=multi, **kw)
+            assert _same_result(a, b), (ci, multi)
+
+
+def test_threaded_run_equals_single_thread_on_workloads(orc):
+    # the 32x32x16 workload (one section) and the 145x145x200 cube of the
+    # next two workloads cropped to 96x96, L=3 (16 sections, seam pass)
+    img, mask = synth.make(1)
+    kw = {k: v for k, v in synth.WORKLOADS[1].params.items() if k != "precision"}
+    assert _same_result(orc.run(img, mask, **kw), orc.run(img, mask, threads=4, **kw))
+    img, mask = synth.make(2)
+    img = np.ascontiguousarray(img[:96, :96])
+    kw = {k: v for k, v in synth.WORKLOADS[2].params.items() if k != "precision"}
+    a = orc.run(img, None, **kw)
+    for t in (2, 5):
+        assert _same_result(a, orc.run(img, None, threads=t, **kw)), t
+    # a masked crop of the 1024x1024x224 cube, L=4 (64 sections)
+    img, mask = synth.make(4, rows=128, cols=128)
+    img = np.ascontiguousarray(img[:, :, :32])
+    kw = dict(rnb_levels=4, spclust_wght=0.1, conv_nregions=12, connectivity=8, n_out_levels=3)
+    assert _same_result(orc.run(img, mask, **kw), orc.run(img, mask, threads=7, **kw))
+
+
+def test_threaded_run_rejects_bad_thread_counts(orc):
+    import ctypes as C
+    img = np.zeros((4, 4, 1), dtype=np.uint16)
+    L = orc.oracle.lib()
+    p = orc.oracle._params(rnb_levels=2)
+    err = C.c_int32(0)
+    for t in (0, -1, 1025):
+        h = L.orc_run_threads(img.ctypes.data, 4, 4, 1, None, C.byref(p), t, C.byref(err))
+        assert not h and err.value == orc.oracle.ORC_EINVAL
