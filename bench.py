@@ -120,6 +120,25 @@ def workload(k, rows=None, cols=None):
     return w, img, mask
 
 
+def oracle_golden(w):
+    """The oracle's stored digests of a whole run of this workload (written by
+    tests/golden/make_full_run_goldens.py), or None for workloads without one
+    (crops)."""
+    p = os.path.join(ROOT, "tests", "golden", f"full_run_{w.name}.json")
+    return json.load(open(p)) if os.path.exists(p) else None
+
+
+def label_exact(seg, golden):
+    """The run's whole output (log, every level, counters) against the
+    oracle's digests: (True, "") or (False, where they first differ)."""
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    import _digest
+    levels = [seg.level(k) for k in range(seg.n_levels())]
+    got = _digest.result_digest(seg.log(), levels, seg.stats())
+    diff = _digest.first_difference(golden, got)
+    return diff == "", diff
+
+
 def cpu_baseline(img, mask, params, target_s=15.0):
     """The oracle as it stands (plain mode: every pair recomputed each
     iteration, single thread), on a bounded sample: the first iterations of
@@ -190,6 +209,9 @@ def main():
     ap.add_argument("--rows", type=int, default=None, help="scaled-down image (profiling); not a bench line")
     ap.add_argument("--cols", type=int, default=None)
     ap.add_argument("--levels", type=int, default=None)
+    ap.add_argument("--profile", type=int, default=1, choices=[0, 1],
+                    help="1: CUDA events around every step kernel (per-kernel times, the roofline's launch "
+                         "times); 0: none, the run as a user makes it")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -215,7 +237,7 @@ def main():
         params["incremental"] = args.incremental
     if args.multi_merge is not None:
         params["multi_merge"] = args.multi_merge
-    params["profile"] = 1
+    params["profile"] = args.profile
     stream = torch.cuda.current_stream()
     img_d = torch.from_numpy(img.view(np.int16)).cuda().view(torch.uint16)
     mask_d = None if mask is None else torch.from_numpy(mask).cuda()
@@ -242,7 +264,38 @@ def main():
     if dist:
         dist.barrier()
     pairs = stats[-1]["pairs"]
+    golden = oracle_golden(w) if (args.rows is None and args.cols is None and args.levels is None
+                                  and not params.get("multi_merge")) else None
+    pairs_source = "library counter (no stored oracle run for this configuration)"
+    exact = None
+    if golden is not None:
+        # the numerator is the oracle's own count for the whole run; the run
+        # must reproduce the oracle's output exactly for the number to count
+        ok, where = label_exact(seg, golden)
+        exact = {"label_exact": ok, "checked": "log, every level's labels/sums/counts, counters vs the oracle's "
+                                               "digests", **({} if ok else {"first_difference": where})}
+        assert golden["stats"]["pairs"] == pairs or not ok, "pair count differs from the oracle's"
+        pairs = golden["stats"]["pairs"]
+        pairs_source = "oracle's full run (stored digests)"
     value = job_rate(world, pairs, args.steps, ms / 1000.0)
+
+    # the same runs without the per-kernel events (profile = 0), to state what
+    # the events cost; not part of the timed region above
+    prof_overhead = None
+    if args.profile == 1 and not args.no_e2e:
+        seg0 = P.RHSEG(img_d, mask_d, stream=stream, **dict(params, profile=0))
+        seg0.run(stream=stream)
+        torch.cuda.synchronize()
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        for _ in range(args.steps):
+            seg0.run(stream=stream)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        seg0.close()
+        ms0 = f0.elapsed_time(f1) / args.steps
+        prof_overhead = {"ms_per_step_profile0": ms0, "ms_per_step_profile1": ms / args.steps,
+                         "overhead_frac": (ms / args.steps - ms0) / ms0}
 
     # dominant kernel: the spectral screen; algorithmic flops 2*B per screened pair
     peaks = load_peaks()
@@ -292,7 +345,14 @@ def main():
                    "candidate_fraction": stats[-1]["candidates"] / max(1, stats[-1]["screened_pairs"]),
                    "candidates_below_threshold": stats[-1]["candidates_below"],
                    "fallbacks": stats[-1]["fallbacks"],
-                   "evaluated_pairs": stats[-1].get("screen_evaluated", 0)},
+                   "evaluated_pairs": stats[-1].get("screen_evaluated", 0),
+                   "useful_over_covered": stats[-1]["screened_pairs"] / max(1, stats[-1].get("screen_evaluated", 0)),
+                   "error_vs_exact": {"max_rel": stats[-1]["screen_err_rel_max"],
+                                      "max_over_bound": stats[-1]["screen_err_bound_max"],
+                                      "rechecked_pairs": stats[-1]["screen_err_pairs"]}},
+        "pairs_source": pairs_source,
+        "parity": exact,
+        "profile_overhead": prof_overhead,
         "level_ms": [round(x, 2) for x in stats[-1]["level_ms"][:params["rnb_levels"]]],
         "level_iters": stats[-1]["level_iters"][:params["rnb_levels"]],
         "level_kernel_ms": {k: [round(x, 1) for x in stats[-1]["level_" + k + "_ms"][:params["rnb_levels"]]]
@@ -305,7 +365,8 @@ def main():
         img_h = torch.from_numpy(img.view(np.int16)).pin_memory()
         mask_h = None if mask is None else torch.from_numpy(mask).pin_memory()
         seg.close()
-        segh = P.RHSEG(img, mask, stream=stream, **params)
+        # the handle a user makes: no per-kernel events
+        segh = P.RHSEG(img, mask, stream=stream, **dict(params, profile=0))
         segh.set_image(img_h, mask_h, stream=stream).run(stream=stream)
         nl = segh.n_levels()
         torch.cuda.synchronize()
@@ -324,7 +385,16 @@ def main():
         segh.close()
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(img, mask, params)
+        cb = cpu_baseline(img, mask, params)
+        if golden is not None:
+            # whole-run time of the plain single-core oracle, extrapolated from
+            # the sample's rate over the run's pairs (not measured), and the
+            # measured whole run of the cached-key oracle on several threads
+            cb["extrapolated_full_run_s"] = golden["stats"]["pairs"] / cb["value"]
+            cb["extrapolation"] = "oracle pairs of the whole run / the sample's pairs/s (plain mode, 1 core)"
+            cb["oracle_cached_full_run"] = {"seconds": golden["wall_s"], "threads": golden["threads"],
+                                            "cpu": golden.get("cpu"), "mode": "cached keys (bit-identical results)"}
+        line["cpu_baseline"] = cb
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:

@@ -75,10 +75,13 @@ typedef struct rhseg_params {
     int32_t n_out_levels;  /* hierarchy snapshots kept at the root; 0 -> 1          */
     int32_t seam_pass;     /* 1: boundary-artifact split pass at each reassembly    */
     int32_t precision;     /* screen of the spectral step (results identical):
-                              0 = FP64 on CUDA cores,
+                              0 = FP64 on CUDA cores (the plain form),
                               1 = FP16 region means on tcgen05 tensor cores, FP32 accumulate,
                               2 = BF16 region means on tcgen05 tensor cores, FP32 accumulate,
-                              3 = FP32 on CUDA cores (the thesis kernel's arithmetic, Fig. 4.8) */
+                              3 = FP32 on CUDA cores (the thesis kernel's arithmetic, Fig. 4.8).
+                              There is no TF32 form: FP16 rows have TF32's unit roundoff
+                              (2^-11) at twice its tensor rate and half its bytes, and the
+                              operand scale 2^-s keeps them inside FP16's range. */
     int32_t profile;       /* 1: time every step kernel with CUDA events (stats *_ms) */
     int32_t incremental;   /* 1: keep every region's exact best non-adjacent partner and
                               recompute only the rows a merge touches, instead of screening
@@ -93,6 +96,13 @@ typedef struct rhseg_params {
                               differ from the single-merge rule (0, default) and match
                               the oracle's multi-merge mode.  Not with incremental = 1
                               (RHSEG_EINVAL). */
+    int64_t wait_cycles;   /* bound, in SM clock cycles, of every wait inside the
+                              tensor-core screen's pipeline (a load or MMA that never
+                              completes, a stalled partner warp); 0 = the default,
+                              4e9 cycles (about 2 s).  A wait that runs out makes the
+                              screen stop, release its tensor memory and set an error
+                              that rhseg_run returns as RHSEG_ETIMEOUT; the handle stays
+                              usable (the next run starts over from the image). */
 } rhseg_params;
 
 /* One merge-log record.  kind 0 = adjacent merge, 1 = spectral merge,
@@ -140,11 +150,23 @@ typedef struct rhseg_stats {
     int64_t screen_evaluated; /* pairs the tensor-core screen's MMAs actually covered
                                  (whole 128x256 units; units whose norm ranges prove
                                  every pair's key >= the threshold are skipped)    */
+    int64_t device_allocs;    /* device allocations (cudaMalloc calls) the library has
+                                 made in this process so far, over all handles; read
+                                 when rhseg_get_stats is called                    */
+    double  screen_err_rel_max;   /* tensor-core screen (precision 1, 2): over the
+                                     re-checked candidate pairs, max |K~ - K| / K, where
+                                     K~ = c 4^s (q_i + q_j - 2 g) is the screen's own
+                                     estimate of the key from its binary32 Gram value g
+                                     and row norms q, and K the exact key; 0 otherwise */
+    double  screen_err_bound_max; /* max |K~ - K| / bound over the same pairs: the
+                                     screen's error model holds iff this is <= 1    */
+    int64_t screen_err_pairs;     /* re-checked pairs the two maxima cover         */
 } rhseg_stats;
 
 typedef struct rhseg_handle rhseg_handle;
 
-/* Create from HOST buffers.  image: [rows][cols][bands] uint16 (copied);
+/* Create from HOST buffers (the hyperspectral cube of Section 4.1, one
+ * region per pixel at the start).  image: [rows][cols][bands] uint16 (copied);
  * mask: [rows][cols], nonzero = no data, or NULL.  Device memory is
  * allocated here (cudaMalloc) and owned by the handle.  The copy runs on
  * `cuda_stream` (a cudaStream_t, NULL = legacy default stream). */
@@ -167,14 +189,27 @@ int rhseg_create_device(const uint16_t *image_dev, int32_t rows, int32_t cols, i
  * RHSEG_ERANGE if the new image breaks the exact-key bound. */
 int rhseg_set_image(rhseg_handle *h, const uint16_t *image, const uint8_t *mask, void *cuda_stream);
 
-/* Run the whole recursion on `cuda_stream` (NULL = the handle's stream) and
- * wait for it.  May be called again; each call recomputes from the image. */
+/* Run the whole recursion (Section 4.1: HSEG steps 1-4 on every section of
+ * the deepest level, then reassembly and HSEG at each level up to the whole
+ * image; Fig. 4.3/4.4) on `cuda_stream` (NULL = the handle's stream) and wait
+ * for it.  May be called again; each call recomputes from the image.
+ * RHSEG_ETIMEOUT when a bounded device wait gave up (see wait_cycles); the
+ * run stops at the next check (at most 32 HSEG iterations later) and its
+ * results are not available (RHSEG_ESTATE from the getters). */
 int rhseg_run(rhseg_handle *h, void *cuda_stream);
+
+/* Change the wait bound of a handle (rhseg_params.wait_cycles; 0 = the
+ * default) for its next runs.  No device work; the paper has no
+ * counterpart (failure detection of this library). */
+int rhseg_set_wait_cycles(rhseg_handle *h, int64_t cycles);
 
 /* Number of hierarchy levels kept at the root (valid after run). */
 int rhseg_n_levels(const rhseg_handle *h, int32_t *n_levels);
 
-/* One hierarchy level, 0 = finest kept ... n_levels-1 = conv_nregions.
+/* One hierarchy level (the output levels of hierarchical segmentation,
+ * Section 4.1, Fig. 4.1:
+ * coarser levels are unions of finer regions), 0 = finest kept ...
+ * n_levels-1 = conv_nregions.
  * labels: host [rows*cols] int32 (0 = masked, 1..R canonical) or NULL;
  * band_sums: host [R*bands] int64 by canonical label or NULL;
  * counts: host [R] int64 or NULL; nregions_out: R (may be NULL).
@@ -194,11 +229,15 @@ int rhseg_get_level(rhseg_handle *h, int32_t level, int32_t *labels, int64_t *ba
  * rhseg_run before.  The paper has no counterpart (it is an interface
  * choice of this library).
  *   labels_dev    [rows*cols] int32 or NULL
- *   band_sums_dev [regions_cap*bands] int64 or NULL (cleared, then filled)
- *   counts_dev    [regions_cap] int64 or NULL (cleared, then filled)
+ *   band_sums_dev [regions_cap*bands] int64 or NULL (first R rows cleared, then filled)
+ *   counts_dev    [regions_cap] int64 or NULL (first R entries cleared, then filled)
  *   nregions_out  host int32: R of this level (may be NULL)
- * RHSEG_ETRUNC if R > regions_cap while sums or counts are requested (R is
- * still returned).  The working array (one int32 per root region) is a
+ * The kernels run on the handle's stream, which does not wait for other
+ * streams: the caller's earlier work on these buffers must be complete
+ * (synchronise the stream that wrote them) before the call.  The current
+ * device must be the one the handle was created on (else RHSEG_EDEVICE).
+ * RHSEG_ETRUNC if R > regions_cap while sums or counts are requested: R is
+ * still returned and no buffer is written.  The working array (one int32 per root region) is a
  * fixed, file-scope device array of RHSEG_NOALLOC_MAX_REGIONS + 1 entries
  * that every GPU using the library holds until the process exits; a root
  * level that started with more regions is rejected with RHSEG_ERANGE.  The
@@ -209,7 +248,8 @@ int rhseg_get_level(rhseg_handle *h, int32_t level, int32_t *labels, int64_t *ba
 int rhseg_get_level_noalloc(rhseg_handle *h, int32_t level, int32_t *labels_dev, int64_t *band_sums_dev,
                             int64_t *counts_dev, int32_t regions_cap, int32_t *nregions_out);
 
-/* Full canonical merge log into host `log` (capacity log_cap records).
+/* Full canonical merge log (every merge of HSEG steps 2-3, Section 4.1, and
+ * every seam split) into host `log` (capacity log_cap records).
  * *log_len receives the number of records; RHSEG_ETRUNC if log_cap is
  * smaller (nothing written).  log may be NULL to query the length. */
 int rhseg_get_log(rhseg_handle *h, rhseg_merge *log, int64_t log_cap, int64_t *log_len);
@@ -221,7 +261,7 @@ void rhseg_destroy(rhseg_handle *h);
 const char *rhseg_strerror(int code);
 const char *rhseg_last_cuda_error(void);
 
-/* Exact keys for explicit region pairs on the device: for t < npairs,
+/* Exact keys (Eq. 1 squared) for explicit region pairs on the device: for t < npairs,
  * out[t] = K(pair_i[t], pair_j[t]) from band sums S (int64 [nreg][bands],
  * row stride `stride` elements) and counts n (int64 [nreg]).  All pointers
  * are device pointers; runs on `cuda_stream` and does not wait. */

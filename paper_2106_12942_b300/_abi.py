@@ -20,7 +20,7 @@ class Params(C.Structure):
         ("rnb_levels", C.c_int32), ("conv_nregions", C.c_int32), ("spclust_wght", C.c_double),
         ("connectivity", C.c_int32), ("min_nregions", C.c_int32), ("n_out_levels", C.c_int32),
         ("seam_pass", C.c_int32), ("precision", C.c_int32), ("profile", C.c_int32), ("incremental", C.c_int32),
-        ("multi_merge", C.c_int32),
+        ("multi_merge", C.c_int32), ("wait_cycles", C.c_int64),
     ]
 
 
@@ -45,7 +45,8 @@ class Stats(C.Structure):
         ("screen_impl", C.c_int32), ("pad", C.c_int32),
         ("level_ms", C.c_double * 6), ("level_iters", C.c_int32 * 6),
         ("level_screen_ms", C.c_double * 6), ("level_adj_ms", C.c_double * 6), ("level_spec_ms", C.c_double * 6),
-        ("screen_evaluated", C.c_int64),
+        ("screen_evaluated", C.c_int64), ("device_allocs", C.c_int64),
+        ("screen_err_rel_max", C.c_double), ("screen_err_bound_max", C.c_double), ("screen_err_pairs", C.c_int64),
     ]
 
 
@@ -64,6 +65,7 @@ SIGNATURES = {
     "rhseg_create_device": (C.c_int, [_VP, C.c_int32, C.c_int32, C.c_int32, _VP, C.POINTER(Params), _VP,
                                       C.POINTER(_VP)]),
     "rhseg_run": (C.c_int, [_VP, _VP]),
+    "rhseg_set_wait_cycles": (C.c_int, [_VP, C.c_int64]),
     "rhseg_set_image": (C.c_int, [_VP, _VP, _VP, _VP]),
     "rhseg_n_levels": (C.c_int, [_VP, C.POINTER(C.c_int32)]),
     "rhseg_get_level": (C.c_int, [_VP, C.c_int32, _VP, _VP, _VP, C.POINTER(C.c_int32)]),

@@ -15,6 +15,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <atomic>
 #include <mutex>
 #include <vector>
 
@@ -32,6 +33,15 @@
 using namespace rhseg;
 
 static thread_local char g_cuda_msg[512] = "";
+
+// Device allocations (cudaMalloc calls) the library has made in this process.
+static std::atomic<int64_t> g_dev_allocs{0};
+
+static cudaError_t dev_malloc(void **p, size_t bytes)
+{
+    g_dev_allocs.fetch_add(1, std::memory_order_relaxed);
+    return cudaMalloc(p, bytes);
+}
 
 #define CK(x)                                                                                   \
     do {                                                                                        \
@@ -63,7 +73,7 @@ struct DBuf {
         p = nullptr;
         n = 0;
         if (count == 0) count = 1;
-        cudaError_t e = cudaMalloc((void **)&p, count * sizeof(T));
+        cudaError_t e = dev_malloc((void **)&p, count * sizeof(T));
         if (e != cudaSuccess) {
             snprintf(g_cuda_msg, sizeof(g_cuda_msg), "cudaMalloc(%zu bytes): %s", count * sizeof(T),
                      cudaGetErrorString(e));
@@ -120,6 +130,7 @@ struct rhseg_handle {
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     int n_sm = 148;
+    int dev = 0;                  // device the handle was created on
     // inputs
     const uint16_t *img = nullptr;
     const uint8_t *mask = nullptr;
@@ -152,7 +163,7 @@ struct rhseg_handle {
     DBuf<unsigned long long> stie, sinit, ckey;
     DBuf<uint8_t> inR;
     DBuf<float> sT, sE, sk, sbuf, srowx;
-    DBuf<float> nlo, nhi;
+    DBuf<float> nlo, nhi, brng;
     DBuf<int32_t> ulist;
     DBuf<unsigned long long> sortk;
     DBuf<IncInfo> sinfo;
@@ -165,9 +176,11 @@ struct rhseg_handle {
     DBuf<int64_t> aoff;
     DBuf<int32_t> Wrow, ref;
     DBuf<uint32_t> cand;
+    DBuf<float> candg, qf;              // screening-error report of the tensor-core forms
     DBuf<SecState> st;
     DBuf<rhseg_merge> log;
     DBuf<int32_t> err, active;
+    DBuf<int32_t> wlist, wcount;        // sections whose operand rows are to be rewritten
     int32_t *active_host = nullptr;
     DBuf<unsigned long long> scan_tmp;
     unsigned long long *scan_host = nullptr;
@@ -203,6 +216,7 @@ static int check_params(const rhseg_params *p, int32_t rows, int32_t cols, int32
     if (p->incremental && p->precision != 3) return RHSEG_EINVAL;   // binary32 rows only
     if (p->multi_merge < 0 || p->multi_merge > 1) return RHSEG_EINVAL;
     if (p->multi_merge && p->incremental) return RHSEG_EINVAL;
+    if (p->wait_cycles < 0) return RHSEG_EINVAL;
     return RHSEG_OK;
 }
 
@@ -387,6 +401,7 @@ static int common_create(rhseg_handle *h, const rhseg_params *p, void *stream)
     h->Bpad = bpad_for(p->precision, h->B);
     int dev = 0;
     CK(cudaGetDevice(&dev));
+    h->dev = dev;
     cudaDeviceProp prop;
     CK(cudaGetDeviceProperties(&prop, dev));
     if (prop.major < 10) {
@@ -432,8 +447,10 @@ static int common_create(rhseg_handle *h, const rhseg_params *p, void *stream)
         // certified norm ranges of the operand rows: units proven empty are skipped
         if ((rc = h->nlo.alloc(h->npos))) return rc;
         if ((rc = h->nhi.alloc(h->npos))) return rc;
+        if ((rc = h->brng.alloc(4 * (h->npos / 128 + 1)))) return rc;
         if ((rc = h->sk.alloc(h->npos))) return rc;
         if ((rc = h->sortk.alloc(2 * P))) return rc;
+        if ((rc = h->qf.alloc(h->npos))) return rc;
     }
     if (p->incremental) {
         if ((rc = h->sbK.alloc(P))) return rc;
@@ -469,8 +486,11 @@ static int common_create(rhseg_handle *h, const rhseg_params *p, void *stream)
     if ((rc = h->ref.alloc((size_t)nsec_max * h->Bs))) return rc;
     if ((rc = h->log.alloc(h->log_cap))) return rc;
     if ((rc = h->err.alloc(1))) return rc;
-    if ((rc = h->active.alloc(1))) return rc;
-    CK(cudaMallocHost((void **)&h->active_host, sizeof(int32_t)));
+    if ((rc = h->wlist.alloc(nsec_max))) return rc;
+    if ((rc = h->wcount.alloc(1))) return rc;
+    CK(cudaMemset(h->wcount.p, 0, 4));
+    if ((rc = h->active.alloc(2))) return rc;
+    CK(cudaMallocHost((void **)&h->active_host, 2 * sizeof(int32_t)));
     CK(cudaMallocHost((void **)&h->scan_host, 2 * sizeof(unsigned long long)));
     return RHSEG_OK;
 }
@@ -549,7 +569,7 @@ extern "C" int rhseg_create_device(const uint16_t *image_dev, int32_t rows, int3
     h->rows = rows; h->cols = cols; h->B = bands;
     if ((rc = common_create(h, p, cuda_stream))) { rhseg_destroy(h); return rc; }
     unsigned long long *tmp = nullptr, host[2] = {0, 0};
-    cudaError_t e = cudaMalloc((void **)&tmp, 16);
+    cudaError_t e = dev_malloc((void **)&tmp, 16);
     if (e == cudaSuccess) e = cudaMemsetAsync(tmp, 0, 16, h->stream);
     if (e == cudaSuccess) {
         k_scan_device_inputs<<<h->n_sm * 4, 256, 0, h->stream>>>(image_dev, mask_dev, (int64_t)rows * cols, bands,
@@ -634,7 +654,8 @@ __global__ void k_scan_inputs_dev(const uint16_t *img, const uint8_t *mask, int6
 // run
 // ---------------------------------------------------------------------------
 
-__global__ void k_count_active(const SecState *st, int nsec, int32_t *active)
+// Sections still running -> active[0]; the device error word -> active[1].
+__global__ void k_count_active(const SecState *st, int nsec, int32_t *active, const int32_t *err)
 {
     int c = 0;
     for (int s = threadIdx.x; s < nsec; s += blockDim.x) c += st[s].done ? 0 : 1;
@@ -645,7 +666,8 @@ __global__ void k_count_active(const SecState *st, int nsec, int32_t *active)
     if (threadIdx.x == 0) {
         int t = 0;
         for (int i = 0; i < (int)(blockDim.x >> 5); i++) t += w[i];
-        *active = t;
+        active[0] = t;
+        active[1] = *(volatile const int32_t *)err;
     }
 }
 
@@ -702,6 +724,14 @@ static void launch_srow_update(rhseg_handle *h, const LevelDev &D)
         e = cudaGetLastError();
     }
     if (e != cudaSuccess) h->launch_err = e;
+}
+
+// Return code of a device error word: a bounded wait of the screen that gave
+// up is RHSEG_ETIMEOUT, any other failed device check RHSEG_ECUDA.
+static int err_word_code(int32_t w)
+{
+    if (w == 0x54435754 || w == 0x54434c44) return RHSEG_ETIMEOUT;
+    return RHSEG_ECUDA;
 }
 
 static int run_impl(rhseg_handle *h)
@@ -802,8 +832,10 @@ static int run_impl(rhseg_handle *h)
         if ((rc = h->adj.alloc((size_t)atot))) return rc;
         int64_t cand_cap = std::min<int64_t>(std::max<int64_t>(maxpairs, 1),
                                              std::max<int64_t>(1 << 16, (1ll << 24) / G.nsec));
-        if (h->p.spclust_wght > 0.0)
+        if (h->p.spclust_wght > 0.0) {
             if ((rc = h->cand.alloc((size_t)G.nsec * cand_cap * 2))) return rc;
+            if (h->qf.p && (rc = h->candg.alloc((size_t)G.nsec * cand_cap))) return rc;
+        }
         const bool inc = h->p.incremental && h->p.spclust_wght > 0.0;
         if (inc)
             if ((rc = h->ckey.alloc((size_t)G.nsec * cand_cap))) return rc;
@@ -823,6 +855,7 @@ static int run_impl(rhseg_handle *h)
         CK(cudaGetLastError());
         LevelDev D{};
         D.level = lev; D.nsec = G.nsec; D.B = h->B; D.Bs = h->Bs; D.Bpad = h->Bpad;
+        D.wait_cycles = h->p.wait_cycles;
         D.precision = h->p.precision;
         D.w = h->p.spclust_wght; D.ww = h->p.spclust_wght * h->p.spclust_wght;
         D.sigma_shift = h->sigma;
@@ -834,9 +867,14 @@ static int run_impl(rhseg_handle *h)
         D.Af = h->Af.p; D.kf = h->kf.p; D.Ad = h->Ad.p; D.kd = h->kd.p;
         D.H = (h->p.precision == 1 || h->p.precision == 2) ? h->H.p : nullptr;
         D.adj = h->adj.p; D.cand = h->cand.p; D.cand_cap = cand_cap;
+        if (h->qf.p && h->p.spclust_wght > 0.0 && !inc) {
+            D.candg = h->candg.p; D.qf = h->qf.p;
+            D.err_gamma = sc.gamma; D.err_u = sc.u; D.err_etaB = sc.eta * std::sqrt((double)h->B);
+        }
         D.log = h->log.p; D.err = h->err.p;
+        D.wlist = h->wlist.p; D.wcount = h->wcount.p;
         if (skip_units) {
-            D.nlo = h->nlo.p; D.nhi = h->nhi.p; D.sk = h->sk.p;
+            D.nlo = h->nlo.p; D.nhi = h->nhi.p; D.sk = h->sk.p; D.brng = h->brng.p;
             D.ulist = h->ulist.p; D.ucap = ucap; D.sortk = h->sortk.p;
         }
         if (h->p.multi_merge) {
@@ -855,10 +893,10 @@ static int run_impl(rhseg_handle *h)
         int32_t target = (lev == 1) ? h->p.conv_nregions : h->min_nr;
         k_init_section<<<G.nsec, STEP_THREADS, 0, s>>>(D, sc, target); h->nlaunch++;
         if (h->p.spclust_wght > 0.0) {
-            k_write_rows<<<h->n_sm * 4, 256, 0, s>>>(D, sc); h->nlaunch++;
+            k_write_rows<<<h->n_sm * 4, 256, 0, s>>>(D, sc, 0); h->nlaunch++;
             if (skip_units) {             // positions in norm order, rows rewritten there
                 k_sort_positions<<<G.nsec, STEP_THREADS, 0, s>>>(D); h->nlaunch++;
-                k_write_rows<<<h->n_sm * 4, 256, 0, s>>>(D, sc); h->nlaunch++;
+                k_write_rows<<<h->n_sm * 4, 256, 0, s>>>(D, sc, 0); h->nlaunch++;
             }
         }
         CK(cudaGetLastError());
@@ -905,16 +943,21 @@ static int run_impl(rhseg_handle *h)
                     if (inc) k_spec_inc<<<G.nsec, STEP_THREADS, 0, s>>>(D, sc);
                     else k_spec_step<<<G.nsec, STEP_THREADS, 0, s>>>(D, sc);
                     h->nlaunch++;
-                    k_write_rows<<<h->n_sm * 4, 256, 0, s>>>(D, sc); h->nlaunch++;
+                    k_write_rows<<<h->n_sm * 4, 256, 0, s>>>(D, sc, 1); h->nlaunch++;
                     if (prof) CK(cudaEventRecord(h->prof_ev[(2 * chunk + k) * 2 + 1], s));
                 }
             }
             CK(cudaGetLastError());
             CK(h->launch_err);
             it += chunk;
-            k_count_active<<<1, 1024, 0, s>>>(h->st.p, G.nsec, h->active.p); h->nlaunch++;
-            CK(cudaMemcpyAsync(h->active_host, h->active.p, 4, cudaMemcpyDeviceToHost, s));
+            k_count_active<<<1, 1024, 0, s>>>(h->st.p, G.nsec, h->active.p, h->err.p); h->nlaunch++;
+            CK(cudaMemcpyAsync(h->active_host, h->active.p, 8, cudaMemcpyDeviceToHost, s));
             CK(cudaStreamSynchronize(s));
+            if (h->active_host[1]) {          // a device wait gave up or a check failed: stop here
+                int rc_err = err_word_code(h->active_host[1]);
+                snprintf(g_cuda_msg, sizeof(g_cuda_msg), "device error word 0x%08x at level %d", h->active_host[1], lev);
+                return rc_err;
+            }
             if (prof) {
                 for (int k = 0; k < chunk; k++) {
                     float a = 0, b = 0, c = 0;
@@ -955,6 +998,12 @@ static int run_impl(rhseg_handle *h)
             h->stats.merges_adj += q.madj;
             h->stats.merges_spec += q.mspec;
             h->stats.seam_splits += q.nsplit;
+            float er, eb;
+            std::memcpy(&er, &q.err_rel_bits, 4);
+            std::memcpy(&eb, &q.err_bnd_bits, 4);
+            h->stats.screen_err_rel_max = std::max(h->stats.screen_err_rel_max, (double)er);
+            h->stats.screen_err_bound_max = std::max(h->stats.screen_err_bound_max, (double)eb);
+            h->stats.screen_err_pairs += q.err_pairs;
         }
         if (lev == 1) h->root_nmerge = sth[0].nmerge;
         {
@@ -985,7 +1034,7 @@ static int run_impl(rhseg_handle *h)
     CK(cudaMemcpy(&errh, h->err.p, 4, cudaMemcpyDeviceToHost));
     if (errh) {
         snprintf(g_cuda_msg, sizeof(g_cuda_msg), "device error word 0x%08x", errh);
-        return RHSEG_ECUDA;
+        return err_word_code(errh);
     }
     // merge counts from the log segments (kind field) are gathered in get_log;
     // per-kind totals here come from a pass over the log lengths
@@ -1029,6 +1078,13 @@ extern "C" int rhseg_run(rhseg_handle *h, void *cuda_stream)
         (void)tot;
     }
     return rc;
+}
+
+extern "C" int rhseg_set_wait_cycles(rhseg_handle *h, int64_t cycles)
+{
+    if (!h || cycles < 0) return RHSEG_EINVAL;
+    h->p.wait_cycles = cycles;
+    return RHSEG_OK;
 }
 
 extern "C" int rhseg_n_levels(const rhseg_handle *h, int32_t *n_levels)
@@ -1093,15 +1149,13 @@ static __device__ __align__(256) int32_t g_level_scratch[RHSEG_NOALLOC_MAX_REGIO
 static int32_t *g_level_scratch_dev[64];     // device address per device, looked up once
 static std::mutex g_level_scratch_mu;
 
-static int level_scratch_ptr(int32_t **out)
+static int level_scratch_ptr(int dev, int32_t **out)
 {
-    int dev = 0;
-    CK(cudaGetDevice(&dev));
     if (dev < 0 || dev >= 64) return RHSEG_EDEVICE;
     std::lock_guard<std::mutex> lock(g_level_scratch_mu);
     if (!g_level_scratch_dev[dev]) {
         void *p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_level_scratch);
+        cudaError_t e = cudaGetSymbolAddress(&p, g_level_scratch);   // for the current device (= dev)
         if (e != cudaSuccess || !p) {
             snprintf(g_cuda_msg, sizeof(g_cuda_msg), "cudaGetSymbolAddress(level scratch): %s", cudaGetErrorString(e));
             return RHSEG_ECUDA;
@@ -1124,8 +1178,14 @@ extern "C" int rhseg_get_level_noalloc(rhseg_handle *h, int32_t level, int32_t *
                  "root level has %d regions; rhseg_get_level_noalloc holds at most %d", m0, RHSEG_NOALLOC_MAX_REGIONS);
         return RHSEG_ERANGE;
     }
+    int cur_dev = -1;
+    CK(cudaGetDevice(&cur_dev));
+    if (cur_dev != h->dev) {
+        snprintf(g_cuda_msg, sizeof(g_cuda_msg), "current device %d is not the handle's device %d", cur_dev, h->dev);
+        return RHSEG_EDEVICE;
+    }
     int32_t *scratch = nullptr;
-    int rc = level_scratch_ptr(&scratch);
+    int rc = level_scratch_ptr(h->dev, &scratch);
     if (rc) return rc;
     int32_t *canon = scratch, *Rdev = scratch + RHSEG_NOALLOC_MAX_REGIONS;
     cudaStream_t s = h->stream;
@@ -1140,16 +1200,14 @@ extern "C" int rhseg_get_level_noalloc(rhseg_handle *h, int32_t level, int32_t *
     CK(cudaMemcpyAsync(&R, Rdev, 4, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     if (nregions_out) *nregions_out = R;
+    // the capacity check comes first: on RHSEG_ETRUNC nothing is written
+    if ((band_sums_dev || counts_dev) && R > regions_cap) return RHSEG_ETRUNC;
     if (labels_dev) {
         k_snap_labels<<<h->n_sm * 8, 256, 0, s>>>(P, h->label.p, h->slot_of_id.p, T.parent.p, T.absorbed_at.p,
                                                   (int32_t)M, canon, labels_dev);
         CK(cudaGetLastError());
     }
     if (band_sums_dev || counts_dev) {
-        if (R > regions_cap) {
-            CK(cudaStreamSynchronize(s));
-            return RHSEG_ETRUNC;
-        }
         if (band_sums_dev && R > 0) CK(cudaMemsetAsync(band_sums_dev, 0, (size_t)R * h->B * 8, s));
         if (counts_dev && R > 0) CK(cudaMemsetAsync(counts_dev, 0, (size_t)R * 8, s));
         if (band_sums_dev && counts_dev) {
@@ -1233,6 +1291,7 @@ extern "C" int rhseg_get_stats(const rhseg_handle *h, rhseg_stats *s)
     if (!h || !s) return RHSEG_EINVAL;
     if (!h->ran) return RHSEG_ESTATE;
     *s = h->stats;
+    s->device_allocs = g_dev_allocs.load(std::memory_order_relaxed);
     return RHSEG_OK;
 }
 
@@ -1249,13 +1308,14 @@ extern "C" void rhseg_destroy(rhseg_handle *h)
     h->slots[0].release(); h->slots[1].release();
     h->sbK.release(); h->sbP.release(); h->srow.release(); h->stie.release(); h->sinit.release();
     h->ckey.release(); h->inR.release(); h->sT.release(); h->sE.release(); h->sk.release(); h->sbuf.release();
-    h->nlo.release(); h->nhi.release(); h->ulist.release();
+    h->nlo.release(); h->nhi.release(); h->brng.release(); h->ulist.release();
     h->sortk.release();
     h->mlist.release(); h->mK.release(); h->mP.release();
     h->srowx.release(); h->sinfo.release();
+    h->candg.release(); h->qf.release();
     h->slot_of_pos.release(); h->X.release(); h->Af.release(); h->kf.release(); h->H.release(); h->Ad.release(); h->kd.release();
     h->adj.release(); h->aoff.release(); h->Wrow.release(); h->ref.release(); h->cand.release(); h->st.release();
-    h->log.release(); h->err.release(); h->active.release();
+    h->log.release(); h->err.release(); h->active.release(); h->wlist.release(); h->wcount.release();
     h->S0.release(); h->n0.release();
     h->snap_canon.release(); h->snap_R.release(); h->snap_labels.release(); h->snap_sums.release();
     h->snap_counts.release(); h->log_out.release();

@@ -40,6 +40,12 @@ struct SecState {
     int32_t npm;
     int32_t nunits;        // tensor-core screen: units kept for this step (the rest are proven empty)
     int64_t evaluated;     // pairs covered by the kept units, accumulated
+    // screening error of the tensor-core screen over the re-checked pairs:
+    // max |K~ - K| / K and max |K~ - K| / bound (binary32 bits, non-negative)
+    uint32_t err_rel_bits, err_bnd_bits;
+    int64_t err_pairs;     // re-checked pairs the two maxima cover
+    int32_t ranges_stale;  // the kept norm ranges of the position blocks need a full recompute
+    int32_t pad2;
 };
 
 // Geometry and buffers of the level in flight (device pointers).  Arrays
@@ -80,9 +86,16 @@ struct LevelDev {
     // candidates
     uint32_t *cand;            // [nsec][cand_cap][2] positions
     int64_t cand_cap;
+    float *candg;              // [nsec][cand_cap] the screen's tested value g - h_j of each
+                               // candidate (tensor-core forms; null otherwise)
+    float *qf;                 // per position: binary32 ||x^||^2 of the operand row (with candg)
+    double err_gamma, err_u, err_etaB;   // the screen's gamma, u and eta sqrt(B) (error report)
     // log
     void *log;                 // rhseg_merge records
     int32_t *err;              // device error word
+    long long wait_cycles;     // bound of the screen's pipeline waits (0: the default)
+    int32_t *wlist;            // [nsec] sections whose positions were rebuilt this iteration
+    int32_t *wcount;           // their number
     // incremental spectral minima (null unless that mode is on)
     int32_t incremental;
     uint64_t *sbK;             // per slot: K bits of the best non-adjacent pair
@@ -94,6 +107,8 @@ struct LevelDev {
     float *sT;                 // per position: the row's binary32 threshold
     float *sE, *sk;            // per position: operand error norm, 4^-sigma / n (both rounded up)
     float *nlo, *nhi;          // per position: bounds of the true norm ||x|| of the row (tensor-core screen)
+    float *brng;               // per 128-position block x 4: kept (min nlo, max nhi, max sk), exact at a
+                               // rebuild and widened by every merge since (tensor-core screen)
     int32_t *ulist;            // [nsec][ucap] kept units of the step, (I << 16) | Jp
     int32_t ucap;
     unsigned long long *sortk; // per slot x 2: scratch of the norm-order sort of the positions
@@ -243,10 +258,21 @@ __device__ __forceinline__ double warp_key(const int64_t *__restrict__ Si, int64
 {
     int lane = threadIdx.x & 31;
     u128 acc = {0, 0};
-    for (int b = lane; b < B; b += 32) {
-        int64_t d = nj * Si[b] - ni * Sj[b];
-        uint64_t a = (uint64_t)(d < 0 ? -d : d);
-        acc = u128_add(acc, u128_sq(a));
+    // four bands per lane loaded together, then accumulated in band order
+    for (int b0 = lane; b0 < B; b0 += 128) {
+        int64_t si[4], sj[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            const int b = b0 + 32 * u;
+            si[u] = (b < B) ? Si[b] : 0;
+            sj[u] = (b < B) ? Sj[b] : 0;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            int64_t d = nj * si[u] - ni * sj[u];
+            uint64_t a = (uint64_t)(d < 0 ? -d : d);
+            acc = u128_add(acc, u128_sq(a));
+        }
     }
     acc = warp_sum_u128(acc);
     double K = 0.0;

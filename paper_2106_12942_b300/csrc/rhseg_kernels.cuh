@@ -325,23 +325,38 @@ __device__ void warp_write_row(const LevelDev &L, int sec, int slot, int pos, co
     const float nf = __int2float_rn((int)n);                 // n < 2^31 (pixels of the image)
     const float rinv = 1.0f / nf;
     float q = 0.0f;
-    for (int b = lane; b < L.Bpad; b += 32) {
-        float x = 0.0f;
-        if (b < L.B) {
-            // |S - n ref| < 2^55: two exact 32-bit halves, one rounding in the fma
-            int64_t v = S[b] - n * (int64_t)ref[b];
-            float xv = fmaf(__int2float_rn((int)(v >> 24)), 16777216.0f, __int2float_rn((int)(v & 0xFFFFFF)));
-            x = xv * rinv * sc.xscale_f;
+    for (int b0 = lane; b0 < L.Bpad; b0 += 256) {
+        // eight bands per lane loaded together (the stores below could alias them)
+        int64_t sv[8];
+        int32_t rv[8];
+#pragma unroll
+        for (int u = 0; u < 8; u++) {
+            const int b = b0 + 32 * u;
+            sv[u] = (b < L.B) ? S[b] : 0;
+            rv[u] = (b < L.B) ? ref[b] : 0;
         }
-        T v = to_op_f<T>(x);
-        X[b] = v;
-        float xd = op_to_f<T>(v);
-        q = fmaf(xd, xd, q);
+#pragma unroll
+        for (int u = 0; u < 8; u++) {
+            const int b = b0 + 32 * u;
+            if (b >= L.Bpad) break;
+            float x = 0.0f;
+            if (b < L.B) {
+                // |S - n ref| < 2^55: two exact 32-bit halves, one rounding in the fma
+                int64_t v = sv[u] - n * (int64_t)rv[u];
+                float xv = fmaf(__int2float_rn((int)(v >> 24)), 16777216.0f, __int2float_rn((int)(v & 0xFFFFFF)));
+                x = xv * rinv * sc.xscale_f;
+            }
+            T v = to_op_f<T>(x);
+            X[b] = v;
+            float xd = op_to_f<T>(v);
+            q = fmaf(xd, xd, q);
+        }
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) q += __shfl_xor_sync(0xffffffffu, q, o);
     if (lane == 0) {
         L.Af[L.poff[sec] + pos] = __fmaf_rd(q, sc.Fq, -sc.E0);
+        if (L.qf != nullptr) L.qf[L.poff[sec] + pos] = q;
         L.kf[L.poff[sec] + pos] = __fdiv_ru(sc.kscale_f, __int2float_rd((int)n));
         if (L.sE != nullptr || L.nlo != nullptr) {
             // operand error norm e >= ||x^ - x|| and 4^-sigma/n (rounded up)
@@ -415,6 +430,7 @@ __global__ void __launch_bounds__(STEP_THREADS) k_init_section(LevelDev L, Scree
         st->nadj = pc / 2;
         st->mc = m0;
         st->rows_from = m0;
+        st->ranges_stale = 1;
         st->npm = 0;
         st->ncand = 0;
         st->nunits = 0;
@@ -478,12 +494,25 @@ __device__ void warp_keys_batch(const LevelDev &L, int64_t ro, const int32_t *pi
             nj[u] = L.n[ro + jj[u]];
         }
         u128 acc[4] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
-        for (int b = lane; b < L.B; b += 32) {
+        // two band steps of the four pairs per round: 16 independent loads in
+        // flight per lane (the region rows mostly come from DRAM)
+        for (int b0 = lane; b0 < L.B; b0 += 64) {
+            const bool two = b0 + 32 < L.B;
+            int64_t si[4][2], sj[4][2];
 #pragma unroll
             for (int u = 0; u < 4; u++) {
-                const int64_t d = nj[u] * Si[u][b] - ni[u] * Sj[u][b];
-                acc[u] = u128_add(acc[u], u128_sq((uint64_t)(d < 0 ? -d : d)));
+                si[u][0] = Si[u][b0];
+                sj[u][0] = Sj[u][b0];
+                si[u][1] = two ? Si[u][b0 + 32] : 0;
+                sj[u][1] = two ? Sj[u][b0 + 32] : 0;
             }
+#pragma unroll
+            for (int u = 0; u < 4; u++)
+#pragma unroll
+                for (int t = 0; t < 2; t++) {
+                    const int64_t d = nj[u] * si[u][t] - ni[u] * sj[u][t];
+                    acc[u] = u128_add(acc[u], u128_sq((uint64_t)(d < 0 ? -d : d)));
+                }
         }
 #pragma unroll
         for (int u = 0; u < 4; u++) {
@@ -753,6 +782,18 @@ __device__ void block_merge(const LevelDev &L, int sec, SecState &st, int a, int
     if (wid == 0) write_row_any(L, sec, a, pa_pos, sc);
     if (tid == 32) mark_pos_dead(L, sec, pb_pos);
     __syncthreads();
+    if (L.brng != nullptr && tid == 0) {
+        // the norm range of a's position block takes in a's new row (b's stays
+        // in its block's range: a wider range only keeps more units)
+        const int64_t gp = L.poff[sec] + pa_pos;
+        float4 *r = (float4 *)L.brng + (gp >> 7);
+        float4 v = *r;
+        v.x = fminf(v.x, L.nlo[gp]);
+        v.y = fmaxf(v.y, L.nhi[gp]);
+        v.z = fmaxf(v.z, L.sk[gp]);
+        *r = v;
+    }
+    __syncthreads();
 }
 
 // ---------------------------------------------------------------------------
@@ -870,6 +911,7 @@ __device__ void block_sort_positions(const LevelDev &L, int sec, SecState &st)
     if (threadIdx.x == 0) {
         st.rows_from = max(st.mc, 1);   // old extent: positions past the new end are marked dead
         st.mc = n;
+        st.ranges_stale = 1;
     }
     __syncthreads();
 }
@@ -877,31 +919,67 @@ __device__ void block_sort_positions(const LevelDev &L, int sec, SecState &st)
 // Compaction that keeps the live positions in their current order (the norm
 // order set at level start; a merged region keeps its position, its new
 // norm close to its parts'), in place (new positions never exceed old ones).
+// Exclusive prefix over the block of one count per thread (whole block);
+// *total gets the sum.  Its first barrier also orders every read before it
+// against the writes after it.
+__device__ __forceinline__ int block_excl_scan(int v, int *total)
+{
+    __shared__ int32_t ws[32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    int incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    __syncthreads();
+    if (lane == 31) ws[wid] = incl;
+    __syncthreads();
+    int off = 0, tot = 0;
+    for (int k = 0; k < nw; k++) {
+        const int w = ws[k];
+        if (k < wid) off += w;
+        tot += w;
+    }
+    *total = tot;
+    return off + incl - v;
+}
+
+constexpr int CP_PER = 16;     // positions per thread per round of a compaction
+
+// Compaction that keeps the live positions in their current order (the norm
+// order set at level start; a merged region keeps its position, its new
+// norm close to its parts'), in place.  Each round gives every thread
+// CP_PER consecutive positions: their slots and liveness are loaded
+// together, one block scan places them, and the writes follow the scan's
+// barrier (a new position never exceeds its old one, and every position of
+// the round was read before any is written).
 __device__ void block_compact_in_order(const LevelDev &L, int sec, SecState &st)
 {
     const int mc = st.mc;
     const int64_t ro = L.roff[sec], pb = L.poff[sec];
-    __shared__ int32_t wcnt[32];
-    __shared__ int32_t base;
-    if (threadIdx.x == 0) base = 0;
-    __syncthreads();
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int c = 0; c < mc; c += blockDim.x) {
-        const int p = c + threadIdx.x;
-        const int slot = (p < mc) ? L.slot_of_pos[pb + p] : -1;
-        const int f = (slot >= 0) ? L.alive[ro + slot] : 0;
-        const unsigned bal = __ballot_sync(0xffffffffu, f);
-        if (lane == 0) wcnt[wid] = __popc(bal);
-        __syncthreads();
-        int off = 0, tot = 0;
-        for (int k = 0; k < nw; k++) { if (k < wid) off += wcnt[k]; tot += wcnt[k]; }
-        if (f) {
-            const int np = base + off + __popc(bal & ((1u << lane) - 1));
-            L.pos_of_slot[ro + slot] = np;
-            L.slot_of_pos[pb + np] = slot;
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) base += tot;
+    int base = 0;
+    for (int c = 0; c < mc; c += blockDim.x * CP_PER) {
+        const int p0 = c + threadIdx.x * CP_PER;
+        int sl[CP_PER];
+        uint8_t f[CP_PER];
+#pragma unroll
+        for (int u = 0; u < CP_PER; u++) sl[u] = (p0 + u < mc) ? L.slot_of_pos[pb + p0 + u] : -1;
+#pragma unroll
+        for (int u = 0; u < CP_PER; u++) f[u] = (sl[u] >= 0) ? L.alive[ro + sl[u]] : 0;
+        int cnt = 0;
+#pragma unroll
+        for (int u = 0; u < CP_PER; u++) cnt += f[u] ? 1 : 0;
+        int tot;
+        int np = base + block_excl_scan(cnt, &tot);
+#pragma unroll
+        for (int u = 0; u < CP_PER; u++)
+            if (f[u]) {
+                L.pos_of_slot[ro + sl[u]] = np;
+                L.slot_of_pos[pb + np] = sl[u];
+                np++;
+            }
+        base += tot;
         __syncthreads();
     }
     if (threadIdx.x == 0) {
@@ -913,34 +991,45 @@ __device__ void block_compact_in_order(const LevelDev &L, int sec, SecState &st)
 
 // New stable position list of the live slots (the screen's operand rows are
 // then rewritten by k_write_rows).
+__device__ void block_compact_stable(const LevelDev &L, int sec, SecState &st);
+
 __device__ void block_compact_positions(const LevelDev &L, int sec, SecState &st)
 {
-    if (L.sortk != nullptr) {
-        block_compact_in_order(L, sec, st);
-        return;
+    if (L.sortk != nullptr) block_compact_in_order(L, sec, st);
+    else block_compact_stable(L, sec, st);
+    // the section's operand rows are rewritten by the next k_write_rows, and
+    // the norm ranges of its position blocks recomputed by the next unit list
+    if (threadIdx.x == 0) {
+        if (L.wcount != nullptr) L.wlist[atomicAdd(L.wcount, 1)] = sec;
+        st.ranges_stale = 1;
     }
+    __syncthreads();
+}
+
+__device__ void block_compact_stable(const LevelDev &L, int sec, SecState &st)
+{
+    // the live slots in slot (= ID) order, rounds as in block_compact_in_order
     const int m0 = st.m0;
     const int64_t ro = L.roff[sec];
-    __shared__ int32_t wcnt[32];
-    __shared__ int32_t base;
-    if (threadIdx.x == 0) base = 0;
-    __syncthreads();
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int c = 0; c < m0; c += blockDim.x) {
-        const int i = c + threadIdx.x;
-        const int f = (i < m0) ? L.alive[ro + i] : 0;
-        const unsigned bal = __ballot_sync(0xffffffffu, f);
-        if (lane == 0) wcnt[wid] = __popc(bal);
-        __syncthreads();
-        int off = 0, tot = 0;
-        for (int k = 0; k < nw; k++) { if (k < wid) off += wcnt[k]; tot += wcnt[k]; }
-        if (f) {
-            const int pos = base + off + __popc(bal & ((1u << lane) - 1));
-            L.pos_of_slot[ro + i] = pos;
-            L.slot_of_pos[L.poff[sec] + pos] = i;
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) base += tot;
+    int base = 0;
+    for (int c = 0; c < m0; c += blockDim.x * CP_PER) {
+        const int i0 = c + threadIdx.x * CP_PER;
+        uint8_t f[CP_PER];
+#pragma unroll
+        for (int u = 0; u < CP_PER; u++) f[u] = (i0 + u < m0) ? L.alive[ro + i0 + u] : 0;
+        int cnt = 0;
+#pragma unroll
+        for (int u = 0; u < CP_PER; u++) cnt += f[u] ? 1 : 0;
+        int tot;
+        int np = base + block_excl_scan(cnt, &tot);
+#pragma unroll
+        for (int u = 0; u < CP_PER; u++)
+            if (f[u]) {
+                L.pos_of_slot[ro + i0 + u] = np;
+                L.slot_of_pos[L.poff[sec] + np] = i0 + u;
+                np++;
+            }
+        base += tot;
         __syncthreads();
     }
     if (threadIdx.x == 0) {
@@ -951,46 +1040,60 @@ __device__ void block_compact_positions(const LevelDev &L, int sec, SecState &st
 }
 
 // Operand rows of every position of the sections whose position list was
-// (re)built this iteration.  A single wave of blocks: every block lists those
-// sections (few per iteration), then the blocks share out (section, chunk)
-// items, 64 chunks per section, one warp per row.
+// (re)built this iteration.  A single wave of blocks: every block takes the
+// list of those sections (from_list: the list the compactions appended to;
+// otherwise a scan of every section, at level start), then the blocks share
+// out (section, chunk) items, one warp per row.  With few sections rebuilt,
+// each gets more chunks, so every warp writes a few rows; with none, every
+// block leaves after one read.
 constexpr int WR_MAX_SECTIONS = 1024;    // 4^5 sections at the deepest of 6 levels
-constexpr int WR_CHUNKS = 64;
+constexpr int WR_CHUNKS = 64;            // chunks per section at least
+constexpr int WR_CHUNKS_MAX = 1024;
 
-__global__ void __launch_bounds__(256) k_write_rows(LevelDev L, ScreenConst sc)
+__global__ void __launch_bounds__(256) k_write_rows(LevelDev L, ScreenConst sc, int from_list)
 {
     __shared__ int32_t list[WR_MAX_SECTIONS];
     __shared__ int32_t wcnt[32];
     __shared__ int32_t nlist;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    if (threadIdx.x == 0) nlist = 0;
+    if (threadIdx.x == 0) nlist = from_list ? min(*(volatile const int32_t *)L.wcount, WR_MAX_SECTIONS) : 0;
     __syncthreads();
-    for (int c = 0; c < L.nsec; c += blockDim.x) {
-        const int sec = c + threadIdx.x;
-        bool f = false;
-        if (sec < L.nsec) {
-            const SecState &st = L.st[sec];
-            f = st.rows_from > 0 && !st.done;
+    if (from_list) {
+        const int n = nlist;
+        if (n == 0) return;                                  // uniform
+        for (int i = threadIdx.x; i < n; i += blockDim.x) list[i] = L.wlist[i];
+        __syncthreads();
+    } else {
+        for (int c = 0; c < L.nsec; c += blockDim.x) {
+            const int sec = c + threadIdx.x;
+            bool f = false;
+            if (sec < L.nsec) {
+                const SecState &st = L.st[sec];
+                f = st.rows_from > 0 && !st.done;
+            }
+            const unsigned bal = __ballot_sync(0xffffffffu, f);
+            if (lane == 0) wcnt[wid] = __popc(bal);
+            __syncthreads();
+            int off = 0, tot = 0;
+            for (int k = 0; k < nw; k++) { if (k < wid) off += wcnt[k]; tot += wcnt[k]; }
+            if (f) list[nlist + off + __popc(bal & ((1u << lane) - 1))] = sec;
+            __syncthreads();
+            if (threadIdx.x == 0) nlist += tot;
+            __syncthreads();
         }
-        const unsigned bal = __ballot_sync(0xffffffffu, f);
-        if (lane == 0) wcnt[wid] = __popc(bal);
-        __syncthreads();
-        int off = 0, tot = 0;
-        for (int k = 0; k < nw; k++) { if (k < wid) off += wcnt[k]; tot += wcnt[k]; }
-        if (f) list[nlist + off + __popc(bal & ((1u << lane) - 1))] = sec;
-        __syncthreads();
-        if (threadIdx.x == 0) nlist += tot;
-        __syncthreads();
     }
-    const int items = nlist * WR_CHUNKS;
+    const int nl = nlist;
+    if (nl == 0) return;
+    const int chunks = min(WR_CHUNKS_MAX, max(WR_CHUNKS, (int)gridDim.x / nl));
+    const int items = nl * chunks;
     for (int it = blockIdx.x; it < items; it += gridDim.x) {
-        const int sec = list[it / WR_CHUNKS], chunk = it % WR_CHUNKS;
+        const int sec = list[it / chunks], chunk = it % chunks;
         const SecState &st = L.st[sec];
         const int old = st.rows_from, mc = st.mc;
         const int pend = ((max(old, mc) + 127) / 128) * 128;
-        const int gw = chunk * nw + wid, ngw = WR_CHUNKS * nw;
+        const int gw = chunk * nw + wid, ngw = chunks * nw;
         for (int pos = gw; pos < mc; pos += ngw) write_row_any(L, sec, L.slot_of_pos[L.poff[sec] + pos], pos, sc);
-        for (int pos = mc + chunk * blockDim.x + threadIdx.x; pos < pend; pos += WR_CHUNKS * blockDim.x)
+        for (int pos = mc + chunk * blockDim.x + threadIdx.x; pos < pend; pos += chunks * blockDim.x)
             mark_pos_dead(L, sec, pos);
     }
 }
@@ -1015,15 +1118,32 @@ __device__ void block_unit_list(const LevelDev &L, int sec, SecState &st, float 
     __shared__ int32_t wsum[32];
     __shared__ int32_t base;
     const bool ranges = nb <= UL_MAX_BLOCKS;
-    if (ranges) {
+    float4 *brng = (L.brng != nullptr) ? (float4 *)L.brng + (pb >> 7) : nullptr;
+    if (ranges && brng != nullptr && !st.ranges_stale) {
+        // the kept ranges (exact at the last rebuild, widened by every merge since)
+        for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+            const float4 r = brng[b];
+            blo[b] = r.x; bhi[b] = r.y; bkm[b] = r.z;
+        }
+    } else if (ranges) {
         for (int b = wid; b < nb; b += nw) {
             float lo = inf, hi = -inf, km = 0.0f;
-            for (int e = lane; e < 128; e += 32) {
-                const int pos = b * 128 + e;
-                if (pos >= mc || !(L.Af[pb + pos] < inf)) continue;   // dead or past the end
-                lo = fminf(lo, L.nlo[pb + pos]);
-                hi = fmaxf(hi, L.nhi[pb + pos]);
-                km = fmaxf(km, L.sk[pb + pos]);
+            float af[4], nl[4], nh[4], kk[4];
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                const int pos = b * 128 + lane + 32 * u;
+                const bool in = pos < mc;
+                af[u] = in ? L.Af[pb + pos] : inf;
+                nl[u] = in ? L.nlo[pb + pos] : inf;
+                nh[u] = in ? L.nhi[pb + pos] : -inf;
+                kk[u] = in ? L.sk[pb + pos] : 0.0f;
+            }
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                if (!(af[u] < inf)) continue;                      // dead or past the end
+                lo = fminf(lo, nl[u]);
+                hi = fmaxf(hi, nh[u]);
+                km = fmaxf(km, kk[u]);
             }
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) {
@@ -1031,40 +1151,38 @@ __device__ void block_unit_list(const LevelDev &L, int sec, SecState &st, float 
                 hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, o));
                 km = fmaxf(km, __shfl_xor_sync(0xffffffffu, km, o));
             }
-            if (lane == 0) { blo[b] = lo; bhi[b] = hi; bkm[b] = km; }
+            if (lane == 0) {
+                blo[b] = lo; bhi[b] = hi; bkm[b] = km;
+                if (brng != nullptr) brng[b] = make_float4(lo, hi, km, 0.0f);
+            }
         }
     }
     if (threadIdx.x == 0) base = 0;
     __syncthreads();
-    // tiles (Ip, Jp), Ip <= Jp, in row-major order; each gives the units
-    // (2 Ip, Jp) and (2 Ip + 1, Jp) (the latter only if that row block exists)
+    // units (I, Jp) with 2 Jp + 1 >= I (the two 128-row halves of every
+    // upper-triangle tile of 256-row blocks), listed row block by row block
+    // (I, then Jp)
     int32_t *ul = L.ulist + (int64_t)sec * L.ucap;
-    const int ntile = nbp * nbp;
-    for (int t0 = 0; t0 < ntile; t0 += blockDim.x) {
+    const int nall = nb * nbp;
+    for (int t0 = 0; t0 < nall; t0 += blockDim.x) {
         const int t = t0 + threadIdx.x;
-        int keep[2] = {0, 0};
-        int Ip = 0, Jp = 0;
-        if (t < ntile) {
-            Ip = t / nbp;
-            Jp = t - Ip * nbp;
-            if (Jp >= Ip) {
-                for (int h = 0; h < 2; h++) {
-                    const int I = 2 * Ip + h;
-                    if (I >= nb) continue;
-                    bool k = !ranges;
-                    for (int c = 0; c < 2 && !k; c++) {
-                        const int J = 2 * Jp + c;
-                        if (J >= nb) continue;
-                        const float gap = fmaxf(0.0f, fmaxf(__fsub_rd(blo[J], bhi[I]), __fsub_rd(blo[I], bhi[J])));
-                        const float klo = __fdiv_rd(__fmul_rd(gap, gap), __fadd_ru(bkm[I], bkm[J]));
-                        k = !(klo >= Tf);                 // empty blocks: infinite gap, dropped
-                    }
-                    keep[h] = k ? 1 : 0;
+        int keep = 0, I = 0, Jp = 0;
+        if (t < nall) {
+            I = t / nbp;
+            Jp = t - I * nbp;
+            if (2 * Jp + 1 >= I) {
+                bool k = !ranges;
+                for (int c = 0; c < 2 && !k; c++) {
+                    const int J = 2 * Jp + c;
+                    if (J >= nb) continue;
+                    const float gap = fmaxf(0.0f, fmaxf(__fsub_rd(blo[J], bhi[I]), __fsub_rd(blo[I], bhi[J])));
+                    const float klo = __fdiv_rd(__fmul_rd(gap, gap), __fadd_ru(bkm[I], bkm[J]));
+                    k = !(klo >= Tf);                 // empty blocks: infinite gap, dropped
                 }
+                keep = k ? 1 : 0;
             }
         }
-        const int cnt = keep[0] + keep[1];
-        int incl = cnt;
+        int incl = keep;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const int v = __shfl_up_sync(0xffffffffu, incl, o);
@@ -1074,14 +1192,13 @@ __device__ void block_unit_list(const LevelDev &L, int sec, SecState &st, float 
         __syncthreads();
         int off = 0, tot = 0;
         for (int k2 = 0; k2 < nw; k2++) { if (k2 < wid) off += wsum[k2]; tot += wsum[k2]; }
-        int w = base + off + incl - cnt;
-        for (int h = 0; h < 2; h++)
-            if (keep[h]) ul[w++] = ((2 * Ip + h) << 16) | Jp;
+        if (keep) ul[base + off + incl - 1] = (I << 16) | Jp;
         __syncthreads();
         if (threadIdx.x == 0) base += tot;
         __syncthreads();
     }
     if (threadIdx.x == 0) {
+        st.ranges_stale = 0;
         st.nunits = base;
         st.evaluated += (int64_t)base * 128 * 256;
     }
@@ -1105,6 +1222,9 @@ __global__ void __launch_bounds__(STEP_THREADS) k_sort_positions(LevelDev L)
 __global__ void __launch_bounds__(STEP_THREADS, 2) k_adj_step(LevelDev L, ScreenConst sc)
 {
     const int sec = blockIdx.x;
+    // a new iteration: the list of sections whose rows are to be rewritten
+    // starts empty (the previous iteration's k_write_rows has finished)
+    if (sec == 0 && threadIdx.x == 0 && L.wcount != nullptr) *L.wcount = 0;
     if (sec >= L.nsec) return;
     __shared__ StepSmem sm;
     if (threadIdx.x == 0) sm.st = L.st[sec];
@@ -1122,13 +1242,22 @@ __global__ void __launch_bounds__(STEP_THREADS, 2) k_adj_step(LevelDev L, Screen
     __syncthreads();
     PairKey best = pk_none();
     if (!L.multi) {
-        for (int i = threadIdx.x; i < m0; i += blockDim.x) {
-            // absorbed slots carry RHSEG_KEY_NONE
-            const uint64_t k = L.bestK[ro + i];
-            const int32_t bp = L.bestP[ro + i];
-            if (k == RHSEG_KEY_NONE) continue;
-            const PairKey c = pk_make(k, i, bp);
-            if (pk_less(c, best)) best = c;
+        for (int i0 = threadIdx.x; i0 < m0; i0 += 8 * blockDim.x) {
+            // eight slots per thread loaded together; absorbed slots carry RHSEG_KEY_NONE
+            uint64_t kk[8];
+            int32_t bp[8];
+#pragma unroll
+            for (int u = 0; u < 8; u++) {
+                const int i = i0 + u * blockDim.x;
+                kk[u] = (i < m0) ? L.bestK[ro + i] : RHSEG_KEY_NONE;
+                bp[u] = (i < m0) ? L.bestP[ro + i] : -1;
+            }
+#pragma unroll
+            for (int u = 0; u < 8; u++) {
+                if (kk[u] == RHSEG_KEY_NONE) continue;
+                const PairKey c = pk_make(kk[u], i0 + u * blockDim.x, bp[u]);
+                if (pk_less(c, best)) best = c;
+            }
         }
         best = block_min_pk(best, sm.pk);
     }
@@ -1174,12 +1303,73 @@ __global__ void __launch_bounds__(STEP_THREADS, 2) k_adj_step(LevelDev L, Screen
         const int pend = ((mc + 255) / 256) * 256;      // the screen reads 256-row column blocks
         const int64_t pb = L.poff[sec];
         const float inf = __int_as_float(0x7f800000);
-        for (int pos = threadIdx.x; pos < pend; pos += blockDim.x)
-            L.H[pb + pos] = (pos < mc) ? 0.5f * (L.Af[pb + pos] - Tf * L.kf[pb + pos]) : inf;
+        for (int p0 = threadIdx.x; p0 < pend; p0 += 4 * blockDim.x) {
+            float a4[4], k4[4];
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                const int pos = p0 + u * blockDim.x;
+                a4[u] = (pos < mc) ? L.Af[pb + pos] : 0.0f;
+                k4[u] = (pos < mc) ? L.kf[pb + pos] : 0.0f;
+            }
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                const int pos = p0 + u * blockDim.x;
+                if (pos < pend) L.H[pb + pos] = (pos < mc) ? 0.5f * (a4[u] - Tf * k4[u]) : inf;
+            }
+        }
         if (L.ulist != nullptr) block_unit_list(L, sec, st, Tf);
     }
     __syncthreads();
     if (threadIdx.x == 0) L.st[sec] = st;
+}
+
+// Screening error of the tensor-core screen on the re-checked candidates of
+// one chunk (entries e < np of sm, keys in sm.pkey): the screen's estimate
+// K~ = c 4^s (q_i + q_j - 2 g) with c = n_i n_j / (n_i + n_j), q the binary32
+// ||x^||^2 of each operand row and g the candidate's binary32 Gram value
+// (the screen stores g - h_j as it tested it; h_j is added back), against
+// the exact K.  The bound on |K~ - K| is
+// c 4^s [gamma (||x^_i|| + ||x^_j||)^2 + e (2 ||x_i - x_j|| + e)], where
+// e = e_i + e_j bounds ||(x^_i - x^_j) - (x_i - x_j)|| (e_i = u ||x^_i|| +
+// eta sqrt(B)) and ||x_i - x_j|| = sqrt(K / c) 2^-s.  The per-section maxima
+// of |K~ - K| / K and |K~ - K| / bound go to st (a report only; no decision
+// uses them).
+__device__ void block_screen_error(const LevelDev &L, int sec, SecState &st, const uint32_t *cand, uint32_t c0,
+                                   int np, StepSmem &sm)
+{
+    const int64_t ro = L.roff[sec], pb = L.poff[sec];
+    const float *g = L.candg + (int64_t)sec * L.cand_cap;
+    const double s4 = (L.sigma_shift && L.precision == 1) ? 4.0 : 1.0;     // 4^sigma (FP16 scaling only)
+    const double sx = (L.sigma_shift && L.precision == 1) ? 0.5 : 1.0;     // 2^-sigma
+    float rel = 0.0f, bnd = 0.0f;
+    for (int e = threadIdx.x; e < np; e += blockDim.x) {
+        // every quantity scaled by n_i + n_j (no binary64 division); the two
+        // ratios and the square roots in binary32 (a report, not a decision)
+        const uint32_t c = c0 + (uint32_t)sm.prow[e];
+        const int pi = (int)cand[2 * c], pj = (int)cand[2 * c + 1];
+        const double K = __longlong_as_double((long long)sm.pkey[e]);
+        const double ni = (double)L.n[ro + sm.pi[e]], nj = (double)L.n[ro + sm.pj[e]];
+        const double nn = ni + nj, pp = ni * nj;
+        const float qi = L.qf[pb + pi], qj = L.qf[pb + pj];
+        // the screen's g: its tested value g - h_j plus h_j (binary64 sum; the
+        // binary32 rounding of g - h_j is far below the bound's gamma term)
+        const double gij = (double)g[c] + (double)L.H[pb + pj];
+        const double Ktn = pp * s4 * ((double)qi + (double)qj - 2.0 * gij);           // K~ (n_i + n_j)
+        const double Kn = K * nn;                                                     // K (n_i + n_j)
+        const float dn = (float)fabs(Ktn - Kn);
+        const float ri = sqrtf(qi), rj = sqrtf(qj);
+        const float ee = (float)L.err_u * (ri + rj) + 2.0f * (float)L.err_etaB;
+        const float dist = sqrtf(__fdiv_ru((float)Kn, (float)pp)) * (float)sx;          // ||x_i - x_j||
+        const float bn = (float)(pp * s4) * ((float)L.err_gamma * (ri + rj) * (ri + rj) + ee * (2.0f * dist + ee));
+        if (K > 0.0) rel = fmaxf(rel, __fdiv_ru(dn, (float)Kn));
+        if (bn > 0.0f) bnd = fmaxf(bnd, __fdiv_ru(dn, bn));
+    }
+    // non-negative binary32 values order as their bits
+    const unsigned rb = __float_as_uint(rel), bb = __float_as_uint(bnd);
+    if (rb) atomicMax(&st.err_rel_bits, rb);
+    if (bb) atomicMax(&st.err_bnd_bits, bb);
+    if (threadIdx.x == 0) st.err_pairs += np;
+    __syncthreads();
 }
 
 // Step 3 of HSEG: exact re-check of the screen's candidates (or of every
@@ -1232,11 +1422,14 @@ __global__ void __launch_bounds__(STEP_THREADS, 2) k_spec_step(LevelDev L, Scree
                     const int idx = atomicAdd(&sm.npair, 1);
                     sm.pi[idx] = min(i, j);
                     sm.pj[idx] = max(i, j);
+                    sm.prow[idx] = (int16_t)(c - c0);       // the entry's candidate
                 }
                 __syncthreads();
                 const int np = sm.npair;
                 block_keys(L, ro, sm.pi, sm.pj, sm.pkey, np);
                 __syncthreads();
+                if (L.candg != nullptr && pass == 0)
+                    block_screen_error(L, sec, st, cand, c0, np, sm);
                 for (int e = tid; e < np; e += nt) {
                     const uint64_t kb = sm.pkey[e];
                     if (!(kb < tbits)) continue;          // K < t (both non-negative binary64)

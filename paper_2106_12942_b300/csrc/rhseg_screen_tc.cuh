@@ -53,7 +53,7 @@ constexpr int TC_EPI_WARP0 = TC_PROD_WARPS + 1;
 constexpr int TC_THREADS = 32 * (TC_PROD_WARPS + 1 + TC_EPI_WARPS);
 static_assert(TC_STAGES % TC_PROD_WARPS == 0, "each producer owns whole ring slots");
 constexpr uint32_t TC_TMEM_COLS = 2 * TC_N;
-constexpr long long TC_WAIT_CYCLES = 4000000000ll;           // about 2 s at 2 GHz
+constexpr long long TC_WAIT_CYCLES = 4000000000ll;           // default wait bound: about 2 s at 2 GHz
 
 // One work unit: rows [rowA, rowA + 128) against rows [rowB, rowB + 256).
 struct TcUnit {
@@ -66,6 +66,7 @@ struct TcShared {
     uint64_t gbar[TC_NGBAR];                  // MMAs of a group of K slices complete
     uint64_t tempty[2];                       // accumulator buffer read out by the epilogue
     uint64_t dfull[TC_NDESC], dempty[TC_NDESC];
+    uint64_t drain;                           // MMAs of an aborted launch complete
     uint32_t tmem_base;
     int abort;
     long long slot_q[TC_STAGES];              // producer only: group that last read each ring slot
@@ -122,13 +123,15 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
         : "memory");
     return ok != 0;
 }
-// Bounded wait: false when the CTA aborted or the wait gave up.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort, int32_t *err)
+// Bounded wait of the pipeline (at most `cycles` clock cycles): false when
+// the CTA aborted or the wait gave up.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort, int32_t *err,
+                                          long long cycles)
 {
     long long t0 = clock64();
     while (!mbar_try_wait(bar, parity)) {
         if (*abort) return false;
-        if (clock64() - t0 > TC_WAIT_CYCLES) {
+        if (clock64() - t0 > cycles) {
             *abort = 1;
             if (err) atomicExch(err, 0x54435754);   // screen wait timed out
             return false;
@@ -138,7 +141,8 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volati
 }
 
 // Bounded wait that ignores the abort flag: used only to let this CTA's own
-// TMA copies land before it exits.
+// TMA copies land, and its own MMAs complete, before it exits (always the
+// default bound: these always finish, and the CTA must not leave before).
 __device__ __forceinline__ void mbar_wait_landed(uint64_t *bar, uint32_t parity, int32_t *err)
 {
     long long t0 = clock64();
@@ -255,6 +259,59 @@ __device__ __forceinline__ void sub2f(float a0, float a1, float b0, float b1, fl
         : "f"(a0), "f"(a1), "f"(b0), "f"(b1));
 }
 
+// Separable test of 64 accumulator columns of one thread's row (half h of
+// its 128 columns of block J): max_j (g_ij - h_j) > h_i over 32 columns at a
+// time (packed differences, 3-input maxima); only a passing chunk is
+// examined element by element, and its passing pairs (upper triangle only
+// on a diagonal block) are appended to the section's candidate list with
+// their tested value g - h_j.
+__device__ __forceinline__ void screen_test_64(const LevelDev &L, SecState *st, int sec, int I, int J, int row,
+                                               bool diag, int h, const uint32_t (&r)[64], const float *hcs, float hr)
+{
+#pragma unroll
+    for (int c0 = 0; c0 < 64; c0 += 32) {
+        const float4 *h4 = (const float4 *)(hcs + h * 64 + c0);
+        float d[32];
+#pragma unroll
+        for (int c = 0; c < 32; c += 4) {
+            const float4 hv = h4[c / 4];
+            sub2f(__uint_as_float(r[c0 + c]), __uint_as_float(r[c0 + c + 1]), hv.x, hv.y, d[c], d[c + 1]);
+            sub2f(__uint_as_float(r[c0 + c + 2]), __uint_as_float(r[c0 + c + 3]), hv.z, hv.w, d[c + 2], d[c + 3]);
+        }
+        if (diag) {
+            // on a diagonal block only the upper triangle holds pairs: the
+            // self pair (which always passes) and the lower triangle are
+            // masked before the test, so their chunks take the fast path
+#pragma unroll
+            for (int c = 0; c < 32; c++)
+                if (h * 64 + c0 + c <= row) d[c] = -__int_as_float(0x7f800000);
+        }
+        float m0 = max3f(d[0], d[1], d[2]), m1 = max3f(d[3], d[4], d[5]);
+        m0 = max3f(m0, d[6], d[7]);   m1 = max3f(m1, d[8], d[9]);
+        m0 = max3f(m0, d[10], d[11]); m1 = max3f(m1, d[12], d[13]);
+        m0 = max3f(m0, d[14], d[15]); m1 = max3f(m1, d[16], d[17]);
+        m0 = max3f(m0, d[18], d[19]); m1 = max3f(m1, d[20], d[21]);
+        m0 = max3f(m0, d[22], d[23]); m1 = max3f(m1, d[24], d[25]);
+        m0 = max3f(m0, d[26], d[27]); m1 = max3f(m1, d[28], d[29]);
+        const float m = max3f(m0, m1, fmaxf(d[30], d[31]));
+        if (m > hr) {
+            for (int c = 0; c < 32; c++) {
+                const int cc = h * 64 + c0 + c;
+                if (!(d[c] > hr)) continue;
+                uint32_t idx = atomicAdd(&st->ncand, 1u);
+                if ((int64_t)idx < L.cand_cap) {
+                    uint32_t *cd = L.cand + ((int64_t)sec * L.cand_cap + idx) * 2;
+                    cd[0] = (uint32_t)(I * TC_TILE + row);
+                    cd[1] = (uint32_t)(J * TC_TILE + cc);
+                    // g - h_j as tested (the re-check adds h_j back for the error report;
+                    // storing g itself would keep all 64 accumulator registers live here)
+                    if (L.candg != nullptr) L.candg[(int64_t)sec * L.cand_cap + idx] = d[c];
+                }
+            }
+        }
+    }
+}
+
 // Work-unit enumeration shared by all roles.  Screen mode: the units of
 // every section with a pending spectral step and a finite threshold (see
 // tc_section_units; unit u of a section is half u & 1 of upper-triangle
@@ -310,6 +367,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_screen_tc(LevelDev L, const _
     TcShared &sh = *(TcShared *)(ring + TC_STAGES * TC_STAGE_BYTES);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int natoms = L.Bpad / TC_KATOM;                       // K slices (pipeline stages) per unit
+    const long long wc = L.wait_cycles > 0 ? L.wait_cycles : TC_WAIT_CYCLES;   // bound of every pipeline wait
 
     long long total;
     if (job.gram_rows > 0) {
@@ -344,6 +402,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_screen_tc(LevelDev L, const _
         for (int g = 0; g < TC_NGBAR; g++) mbar_init(&sh.gbar[g], 1);
         for (int b = 0; b < 2; b++) mbar_init(&sh.tempty[b], TC_EPI_WARPS);
         for (int d = 0; d < TC_NDESC; d++) { mbar_init(&sh.dfull[d], 1); mbar_init(&sh.dempty[d], TC_EPI_WARPS); }
+        mbar_init(&sh.drain, 1);
         sh.abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -385,13 +444,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_screen_tc(LevelDev L, const _
                 }
                 if (kc == 0) {
                     const int ds = (int)(k % TC_NDESC);
-                    if (k >= TC_NDESC && !mbar_wait(&sh.dempty[ds], (uint32_t)((k / TC_NDESC - 1) & 1), abort, L.err))
+                    if (k >= TC_NDESC && !mbar_wait(&sh.dempty[ds], (uint32_t)((k / TC_NDESC - 1) & 1), abort, L.err, wc))
                         break;
                     sh.desc[ds] = u;
                     mbar_arrive(&sh.dfull[ds]);
                 }
                 const long long qo = sh.slot_q[slot];
-                if (qo >= 0 && !mbar_wait(&sh.gbar[qo % TC_NGBAR], (uint32_t)((qo / TC_NGBAR) & 1), abort, L.err)) break;
+                if (qo >= 0 && !mbar_wait(&sh.gbar[qo % TC_NGBAR], (uint32_t)((qo / TC_NGBAR) & 1), abort, L.err, wc)) break;
                 uint8_t *a = ring + slot * TC_STAGE_BYTES;                       // A slice, then B slice
                 uint8_t *b = a + TC_A_BYTES;
                 const int x = kc * TC_KATOM;
@@ -415,20 +474,22 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_screen_tc(LevelDev L, const _
             int slot = 0;
             uint32_t phase = 0;
             long long q = 0;                                     // commit groups issued
+            bool issued = false;
             for (long long k = 0; k < my_units && !*abort; k++) {
                 const int buf = (int)(k & 1);
-                if (!mbar_wait(&sh.tempty[buf], (uint32_t)(((k >> 1) & 1) ^ 1), abort, L.err)) break;
+                if (!mbar_wait(&sh.tempty[buf], (uint32_t)(((k >> 1) & 1) ^ 1), abort, L.err, wc)) break;
                 tc_fence_after();
                 const uint32_t dt = tbase + (uint32_t)(buf * TC_N);
                 bool ok = true;
                 for (int kc = 0; kc < natoms; kc++) {
-                    if (!mbar_wait(&sh.full[slot], phase, abort, L.err)) { ok = false; break; }
+                    if (!mbar_wait(&sh.full[slot], phase, abort, L.err, wc)) { ok = false; break; }
                     tc_fence_after();
                     const uint32_t a = smem_u32(ring + slot * TC_STAGE_BYTES);
                     const uint64_t ad = sdesc_sw64(a), bd = sdesc_sw64(a + TC_A_BYTES);
 #pragma unroll
                     for (int kk = 0; kk < TC_KATOM / 16; kk++)
                         tc_mma(dt, ad + (uint64_t)(2 * kk), bd + (uint64_t)(2 * kk), idesc, (kc > 0 || kk > 0) ? 1u : 0u);
+                    issued = true;
                     if (++slot == TC_STAGES) { slot = 0; phase ^= 1; }
                     if ((kc + 1) % G == 0 || kc + 1 == natoms) {
                         tc_commit(&sh.gbar[q % TC_NGBAR]);          // releases the group's slots; the
@@ -436,6 +497,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_screen_tc(LevelDev L, const _
                     }
                 }
                 if (!ok) break;
+            }
+            // an aborted launch may leave MMAs in flight: they complete
+            // before the tensor memory is released
+            if (*abort && issued) {
+                tc_commit(&sh.drain);
+                mbar_wait_landed(&sh.drain, 0, L.err);
             }
         }
         __syncwarp();
@@ -453,7 +520,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_screen_tc(LevelDev L, const _
         const float inf = __int_as_float(0x7f800000);
         float hc_next = inf, hr_next = inf;
         TcUnit nxt{};
-        bool ok0 = mbar_wait(&sh.dfull[0], 0, abort, L.err);
+        bool ok0 = mbar_wait(&sh.dfull[0], 0, abort, L.err, wc);
         if (ok0) {
             nxt = sh.desc[0];
             __syncwarp();
@@ -472,7 +539,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_screen_tc(LevelDev L, const _
             asm volatile("bar.sync 1, %0;" ::"n"(TC_EPI_WARPS * 32) : "memory");
             if (k + 1 < my_units) {
                 const int ds = (int)((k + 1) % TC_NDESC);
-                if (mbar_wait(&sh.dfull[ds], (uint32_t)(((k + 1) / TC_NDESC) & 1), abort, L.err)) {
+                if (mbar_wait(&sh.dfull[ds], (uint32_t)(((k + 1) / TC_NDESC) & 1), abort, L.err, wc)) {
                     nxt = sh.desc[ds];
                     __syncwarp();
                     if (lane == 0) mbar_arrive(&sh.dempty[ds]);
@@ -483,7 +550,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_screen_tc(LevelDev L, const _
                 }
             }
             const long long ql = k * gpu + gpu - 1;          // the unit's last commit group
-            bool ok = mbar_wait(&sh.gbar[ql % TC_NGBAR], (uint32_t)((ql / TC_NGBAR) & 1), abort, L.err);
+            bool ok = mbar_wait(&sh.gbar[ql % TC_NGBAR], (uint32_t)((ql / TC_NGBAR) & 1), abort, L.err, wc);
             ok = __all_sync(0xffffffffu, ok);
             if (!ok) continue;                               // the next loop top stops every warp
             tc_fence_after();
@@ -516,39 +583,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_screen_tc(LevelDev L, const _
                     for (int c = 0; c < 64; c++) o[c] = __uint_as_float(r[c]);
                     continue;
                 }
-#pragma unroll
-                for (int c0 = 0; c0 < 64; c0 += 32) {
-                    const float4 *h4 = (const float4 *)(hcs + h * 64 + c0);
-                    float d[32];
-#pragma unroll
-                    for (int c = 0; c < 32; c += 4) {
-                        const float4 hv = h4[c / 4];
-                        sub2f(__uint_as_float(r[c0 + c]), __uint_as_float(r[c0 + c + 1]), hv.x, hv.y, d[c], d[c + 1]);
-                        sub2f(__uint_as_float(r[c0 + c + 2]), __uint_as_float(r[c0 + c + 3]), hv.z, hv.w, d[c + 2],
-                              d[c + 3]);
-                    }
-                    float m0 = max3f(d[0], d[1], d[2]), m1 = max3f(d[3], d[4], d[5]);
-                    m0 = max3f(m0, d[6], d[7]);   m1 = max3f(m1, d[8], d[9]);
-                    m0 = max3f(m0, d[10], d[11]); m1 = max3f(m1, d[12], d[13]);
-                    m0 = max3f(m0, d[14], d[15]); m1 = max3f(m1, d[16], d[17]);
-                    m0 = max3f(m0, d[18], d[19]); m1 = max3f(m1, d[20], d[21]);
-                    m0 = max3f(m0, d[22], d[23]); m1 = max3f(m1, d[24], d[25]);
-                    m0 = max3f(m0, d[26], d[27]); m1 = max3f(m1, d[28], d[29]);
-                    const float m = max3f(m0, m1, fmaxf(d[30], d[31]));
-                    if (m > hr) {
-                        for (int c = 0; c < 32; c++) {
-                            const int cc = h * 64 + c0 + c;
-                            if (!(d[c] > hr)) continue;
-                            if (diag && cc <= row) continue;
-                            uint32_t idx = atomicAdd(&st->ncand, 1u);
-                            if ((int64_t)idx < L.cand_cap) {
-                                uint32_t *cd = L.cand + ((int64_t)cur.sec * L.cand_cap + idx) * 2;
-                                cd[0] = (uint32_t)(cur.I * TC_TILE + row);
-                                cd[1] = (uint32_t)(J * TC_TILE + cc);
-                            }
-                        }
-                    }
-                }
+                screen_test_64(L, st, cur.sec, cur.I, J, row, diag, h, r, hcs, hr);
             }
         }
     }

@@ -16,7 +16,9 @@ merges in every form: 1 FP16 tensor cores, 2 BF16 tensor cores, 3 FP32, 0
 FP64); incremental (1: exact per-region spectral minima, precision 3 only,
 same merges); multi_merge (1: all mutually best pairs per stage merge in one
 iteration, a different rule with its own oracle mode); profile (1: per-kernel
-CUDA-event times in stats()).
+CUDA-event times in stats()); wait_cycles (bound of the tensor-core screen's
+pipeline waits in clock cycles, 0 = the default of about 2 s; a wait that
+runs out makes run() raise RHSEGError with code RHSEG_ETIMEOUT).
 """
 from __future__ import annotations
 
@@ -28,7 +30,7 @@ from . import _abi
 
 DEFAULTS = dict(rnb_levels=1, conv_nregions=1, spclust_wght=0.0, connectivity=8, min_nregions=0,
                 n_out_levels=1, seam_pass=1, precision=1, profile=0, incremental=0,
-                multi_merge=0)
+                multi_merge=0, wait_cycles=0)
 
 
 class RHSEGError(RuntimeError):
@@ -105,6 +107,12 @@ class RHSEG:
         self._keep_host = (image, mask)
         _check(self._lib.rhseg_set_image(self._h, C.c_void_p(ptr), None if mptr is None else C.c_void_p(mptr),
                                          _stream_ptr(stream)), "rhseg_set_image")
+        return self
+
+    def set_wait_cycles(self, cycles: int):
+        """Bound of the tensor-core screen's pipeline waits for the next runs
+        (0 = the default)."""
+        _check(self._lib.rhseg_set_wait_cycles(self._h, int(cycles)), "rhseg_set_wait_cycles")
         return self
 
     def run(self, stream=None):

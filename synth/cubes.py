@@ -58,7 +58,7 @@ WORKLOADS = {
     2: Workload("rhseg_145x145x200_fp64", 145, 145, 200, 120, 16, 80.0, 10000, 0.0, False,
                 dict(rnb_levels=3, spclust_wght=0.2, conv_nregions=16, connectivity=8, precision=0)),
     3: Workload("rhseg_145x145x200_mixed", 145, 145, 200, 120, 16, 80.0, 10000, 0.0, False,
-                dict(rnb_levels=3, spclust_wght=0.2, conv_nregions=16, connectivity=8, precision=1)),
+                dict(rnb_levels=3, spclust_wght=0.2, conv_nregions=16, connectivity=8, precision=2)),
     4: Workload("rhseg_1024x1024x224_mixed", 1024, 1024, 224, 3000, 64, 100.0, 10000, 0.1, False,
                 dict(rnb_levels=5, spclust_wght=0.1, conv_nregions=64, connectivity=8, precision=1)),
     5: Workload("rhseg_2048x2048x128_mixed", 2048, 2048, 128, 12000, 128, 60.0, 16383, 0.0, True,

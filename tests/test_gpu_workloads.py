@@ -1,12 +1,17 @@
 """Parity at the full workload sizes.
 
 145x145x200 (L=3): the whole run is compared with the oracle (about 40 s of
-CPU), for the FP64 screen and the FP16 tensor-core screen.
-1024x1024x224 (L=5, the benchmark's workload, same launch configuration as
-bench.py): the oracle cannot replay the whole recursion in test time, so the
-first iterations of sampled deepest-level sections (which are independent of
-each other) are compared record by record, and properties that hold at any
-size are checked on the final output."""
+CPU), for every screen form: FP64 and FP32 on CUDA cores, FP16 and BF16 (the
+mixed-precision workload's form) on the tensor cores, whose per-run
+screening-error report must stay within its bound.
+1024x1024x224 (L=5, the benchmark's workload and launch configuration) and
+2048x2048x128 (L=6): the whole output (every log record, every hierarchy
+level's labels, sums and counts, the counters) is compared with digests of
+the oracle's run, stored by tests/golden/make_full_run_goldens.py (the
+oracle takes CPU-hours there).  The sampled checks below them compare the
+first iterations of chosen deepest-level sections record by record and
+check properties that hold at any size; they localise a difference."""
+import json
 import os
 import sys
 
@@ -15,7 +20,10 @@ import pytest
 
 sys.path.insert(0, os.path.dirname(__file__))
 import synth  # noqa: E402
+import _digest  # noqa: E402
 from test_gpu_parity import _assert_same  # noqa: E402
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
 pytestmark = pytest.mark.gpu
 
@@ -36,7 +44,7 @@ def cfg2(orc):
     return img, mask, kw, orc.run(img, mask, **kw)
 
 
-@pytest.mark.parametrize("precision", [1, 3, 0])
+@pytest.mark.parametrize("precision", [2, 1, 3, 0])
 def test_rhseg_145x145x200(P, cfg2, precision):
     img, mask, kw, ref = cfg2
     seg = P.RHSEG(img, mask, precision=precision, **kw)
@@ -45,6 +53,33 @@ def test_rhseg_145x145x200(P, cfg2, precision):
     st = seg.stats()
     if precision in (1, 2):
         assert st["candidates"] <= st["screened_pairs"]
+        # per-run screening error over the re-checked pairs, within its bound
+        assert st["screen_err_pairs"] > 0
+        assert 0.0 < st["screen_err_bound_max"] <= 1.0, st["screen_err_bound_max"]
+        assert st["screen_err_rel_max"] > 0.0
+
+
+def _gpu_digest(seg):
+    levels = [seg.level(k) for k in range(seg.n_levels())]
+    return _digest.result_digest(seg.log(), levels, seg.stats())
+
+
+@pytest.mark.parametrize("k,precision", [(4, 1), (4, 2), (5, 1)])
+def test_full_run_equals_oracle(P, k, precision):
+    """Every record, level and counter of a whole run at full size against the
+    oracle's stored digests."""
+    w = synth.WORKLOADS[k]
+    path = os.path.join(GOLDEN, f"full_run_{w.name}.json")
+    want = json.load(open(path))
+    img, mask = synth.make(k)
+    kw = dict(w.params, precision=precision)
+    assert want["params"] == {a: b for a, b in kw.items() if a != "precision"}
+    seg = P.RHSEG(img, mask, **kw)
+    seg.run()
+    got = _gpu_digest(seg)
+    seg.close()
+    diff = _digest.first_difference(want, got)
+    assert diff == "", f"{w.name} p{precision}: {diff}"
 
 
 @pytest.fixture(scope="module")

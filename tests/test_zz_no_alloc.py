@@ -29,7 +29,11 @@ def P():
     return P
 
 
-def _noalloc(P, seg, level, cap):
+def _noalloc(P, seg, level, cap, want=("labels", "sums", "counts")):
+    """One call with the requested outputs (the others passed as NULL).  The
+    buffers are filled with -7 on torch's stream first; the library runs on
+    the handle's own stream, so torch's fill is completed before the call,
+    as the header asks of every caller."""
     import torch
     from paper_2106_12942_b300 import _abi
     L = _abi.load()
@@ -37,9 +41,14 @@ def _noalloc(P, seg, level, cap):
     lab = torch.full((rows, cols), -7, dtype=torch.int32, device="cuda")
     sums = torch.full((max(cap, 1), bands), -7, dtype=torch.int64, device="cuda")
     cnt = torch.full((max(cap, 1),), -7, dtype=torch.int64, device="cuda")
+    torch.cuda.synchronize()
     R = C.c_int32(-1)
-    rc = L.rhseg_get_level_noalloc(seg._h, level, C.c_void_p(lab.data_ptr()), C.c_void_p(sums.data_ptr()),
-                                   C.c_void_p(cnt.data_ptr()), cap, C.byref(R))
+
+    def ptr(name, t):
+        return C.c_void_p(t.data_ptr()) if name in want else None
+
+    rc = L.rhseg_get_level_noalloc(seg._h, level, ptr("labels", lab), ptr("sums", sums), ptr("counts", cnt), cap,
+                                   C.byref(R))
     return rc, R.value, lab.cpu().numpy(), sums.cpu().numpy(), cnt.cpu().numpy()
 
 
@@ -50,10 +59,12 @@ def test_noalloc_levels_equal_get_level_twice(P):
     seg.run()
     n = seg.n_levels()
     assert n >= 2
+    want = [seg.level(k) for k in range(n)]      # rhseg_get_level (which allocates), before counting
+    allocs0 = seg.stats()["device_allocs"]
     order = list(range(n)) + list(reversed(range(n)))    # every level, then again in the other order
     for _call in range(2):
         for k in order:
-            lab, sums, cnt = seg.level(k)
+            lab, sums, cnt = want[k]
             R = len(cnt)
             rc, Rn, labn, sumsn, cntn = _noalloc(P, seg, k, R + 3)
             assert rc == 0
@@ -62,10 +73,28 @@ def test_noalloc_levels_equal_get_level_twice(P):
             assert np.array_equal(sumsn[:R], sums)
             assert np.array_equal(cntn[:R], cnt)
             assert np.all(cntn[R:] == -7)          # nothing written past R
-    # labels only, and a too-small table buffer
-    lab, sums, cnt = seg.level(n - 1)
-    rc, Rn, _, _, _ = _noalloc(P, seg, n - 1, len(cnt) - 1)
-    assert rc == -7 and Rn == len(cnt)           # RHSEG_ETRUNC, R still reported
+            assert np.all(sumsn[R:] == -7)
+    # one table only, and labels only (the other outputs NULL)
+    k = n // 2
+    lab, sums, cnt = want[k]
+    R = len(cnt)
+    rc, Rn, labn, sumsn, cntn = _noalloc(P, seg, k, R, want=("sums",))
+    assert rc == 0 and Rn == R and np.array_equal(sumsn[:R], sums)
+    assert np.all(labn == -7) and np.all(cntn == -7)
+    rc, Rn, labn, sumsn, cntn = _noalloc(P, seg, k, R, want=("counts",))
+    assert rc == 0 and Rn == R and np.array_equal(cntn[:R], cnt)
+    assert np.all(labn == -7) and np.all(sumsn == -7)
+    rc, Rn, labn, sumsn, cntn = _noalloc(P, seg, k, 0, want=("labels",))
+    assert rc == 0 and Rn == R and np.array_equal(labn, lab)
+    rc, Rn, labn, sumsn, cntn = _noalloc(P, seg, k, 0, want=())
+    assert rc == 0 and Rn == R and np.all(labn == -7)
+    # a too-small table buffer: RHSEG_ETRUNC, R still reported, nothing written
+    lab, sums, cnt = want[n - 1]
+    rc, Rn, labn, sumsn, cntn = _noalloc(P, seg, n - 1, len(cnt) - 1)
+    assert rc == -7 and Rn == len(cnt)
+    assert np.all(labn == -7) and np.all(sumsn == -7) and np.all(cntn == -7)
+    # none of these calls allocated device memory in the library
+    assert seg.stats()["device_allocs"] == allocs0
     seg.close()
 
 
