@@ -70,6 +70,8 @@ def test_full_run_equals_oracle(P, k, precision):
     oracle's stored digests."""
     w = synth.WORKLOADS[k]
     path = os.path.join(GOLDEN, f"full_run_{w.name}.json")
+    if not os.path.exists(path):
+        pytest.skip(f"the oracle's digests of {w.name} are not stored (tests/golden/make_full_run_goldens.py {k})")
     want = json.load(open(path))
     img, mask = synth.make(k)
     kw = dict(w.params, precision=precision)
