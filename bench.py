@@ -209,6 +209,11 @@ def main():
     ap.add_argument("--rows", type=int, default=None, help="scaled-down image (profiling); not a bench line")
     ap.add_argument("--cols", type=int, default=None)
     ap.add_argument("--levels", type=int, default=None)
+    ap.add_argument("--autotune", type=int, default=1, choices=[0, 1],
+                    help="1: the screen schedule the autotuner stored for this band count and section size "
+                         "(paper_2106_12942_b300/autotune_cache.json), if any")
+    ap.add_argument("--overlap", type=int, default=0, choices=[0, 1],
+                    help="1: the even and odd sections of a level on two overlapping streams")
     ap.add_argument("--profile", type=int, default=1, choices=[0, 1],
                     help="1: CUDA events around every step kernel (per-kernel times, the roofline's launch "
                          "times); 0: none, the run as a user makes it")
@@ -238,7 +243,17 @@ def main():
     if args.multi_merge is not None:
         params["multi_merge"] = args.multi_merge
     params["profile"] = args.profile
-    stream = torch.cuda.current_stream()
+    params["overlap"] = args.overlap
+    tuned = {}
+    if args.autotune and params.get("precision") in (1, 2):
+        from paper_2106_12942_b300 import autotune
+        sec_px = autotune.deepest_section_px(w.rows, w.cols, params["rnb_levels"])
+        tuned = autotune.lookup(w.bands, sec_px)
+        params.update(tuned)
+    # a stream of our own (the legacy default stream cannot be captured as a
+    # CUDA graph, which the library does for runs without per-kernel events)
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
     img_d = torch.from_numpy(img.view(np.int16)).cuda().view(torch.uint16)
     mask_d = None if mask is None else torch.from_numpy(mask).cuda()
     seg = P.RHSEG(img_d, mask_d, stream=stream, **params)
@@ -351,6 +366,7 @@ def main():
                                       "max_over_bound": stats[-1]["screen_err_bound_max"],
                                       "rechecked_pairs": stats[-1]["screen_err_pairs"]}},
         "pairs_source": pairs_source,
+        "autotune": tuned or "no stored choice (library defaults)",
         "parity": exact,
         "profile_overhead": prof_overhead,
         "level_ms": [round(x, 2) for x in stats[-1]["level_ms"][:params["rnb_levels"]]],

@@ -198,7 +198,9 @@ struct rhseg_handle {
     DBuf<rhseg_merge> log_out;
     // instrumentation
     int64_t nlaunch = 0, nscreen = 0;
-    std::vector<cudaEvent_t> prof_ev;   // [3 kernels][chunk][2]
+    std::vector<cudaEvent_t> prof_ev;   // [group][3 kernels][chunk][2]
+    cudaStream_t stream2 = nullptr;     // second group's stream (two-group overlap)
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     CUtensorMap tmap;                   // operand rows of the tensor-core screen
     cudaError_t launch_err = cudaSuccess;
 };
@@ -217,6 +219,8 @@ static int check_params(const rhseg_params *p, int32_t rows, int32_t cols, int32
     if (p->multi_merge < 0 || p->multi_merge > 1) return RHSEG_EINVAL;
     if (p->multi_merge && p->incremental) return RHSEG_EINVAL;
     if (p->wait_cycles < 0) return RHSEG_EINVAL;
+    if (p->screen_group < 0 || p->screen_group > 8) return RHSEG_EINVAL;
+    if (p->overlap < 0 || p->overlap > 1) return RHSEG_EINVAL;
     return RHSEG_OK;
 }
 
@@ -473,6 +477,7 @@ static int common_create(rhseg_handle *h, const rhseg_params *p, void *stream)
         if ((rc = h->mP.alloc(P))) return rc;
     }
     if (screen_uses_tcgen05(p->precision)) {
+        CK(screen_tc_prepare(p->precision));
         int mr = make_operand_map(&h->tmap, h->X.p, (int64_t)h->npos, h->Bpad, p->precision);
         if (mr) {
             snprintf(g_cuda_msg, sizeof(g_cuda_msg), "tensor map for the screen operands failed (%d)", mr);
@@ -486,9 +491,12 @@ static int common_create(rhseg_handle *h, const rhseg_params *p, void *stream)
     if ((rc = h->ref.alloc((size_t)nsec_max * h->Bs))) return rc;
     if ((rc = h->log.alloc(h->log_cap))) return rc;
     if ((rc = h->err.alloc(1))) return rc;
-    if ((rc = h->wlist.alloc(nsec_max))) return rc;
-    if ((rc = h->wcount.alloc(1))) return rc;
-    CK(cudaMemset(h->wcount.p, 0, 4));
+    if ((rc = h->wlist.alloc(2 * (size_t)nsec_max))) return rc;
+    if ((rc = h->wcount.alloc(2))) return rc;
+    CK(cudaMemset(h->wcount.p, 0, 8));
+    CK(cudaStreamCreateWithFlags(&h->stream2, cudaStreamNonBlocking));
+    CK(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
     if ((rc = h->active.alloc(2))) return rc;
     CK(cudaMallocHost((void **)&h->active_host, 2 * sizeof(int32_t)));
     CK(cudaMallocHost((void **)&h->scan_host, 2 * sizeof(unsigned long long)));
@@ -671,17 +679,17 @@ __global__ void k_count_active(const SecState *st, int nsec, int32_t *active, co
     }
 }
 
-static void launch_screen(rhseg_handle *h, const LevelDev &L)
+static void launch_screen(rhseg_handle *h, const LevelDev &L, cudaStream_t st)
 {
     h->nlaunch++;
     h->nscreen++;
     int grid = h->n_sm * 2;
     switch (h->p.precision) {
-    case 0: k_screen_simt<double, double><<<grid, 256, 0, h->stream>>>(L); break;
-    case 3: k_screen_simt<float, float><<<grid, 256, 0, h->stream>>>(L); break;
+    case 0: k_screen_simt<double, double><<<grid, 256, 0, st>>>(L); break;
+    case 3: k_screen_simt<float, float><<<grid, 256, 0, st>>>(L); break;
     default: {
         TcJob job{0, nullptr};
-        cudaError_t e = launch_screen_tc_map(L, h->tmap, h->p.precision, h->n_sm, h->stream, job);
+        cudaError_t e = launch_screen_tc_map(L, h->tmap, h->p.precision, h->n_sm, st, job);
         if (e != cudaSuccess) h->launch_err = e;
         break;
     }
@@ -747,7 +755,7 @@ static int run_impl(rhseg_handle *h)
     h->nscreen = 0;
     const int chunk = 32;
     if (h->p.profile && h->prof_ev.empty()) {
-        h->prof_ev.resize(3 * chunk * 2);
+        h->prof_ev.resize(2 * 3 * chunk * 2);
         for (auto &e : h->prof_ev) CK(cudaEventCreate(&e));
     }
     h->seglen.assign(L + 1, {});
@@ -856,6 +864,7 @@ static int run_impl(rhseg_handle *h)
         LevelDev D{};
         D.level = lev; D.nsec = G.nsec; D.B = h->B; D.Bs = h->Bs; D.Bpad = h->Bpad;
         D.wait_cycles = h->p.wait_cycles;
+        D.tc_group = h->p.screen_group;
         D.precision = h->p.precision;
         D.w = h->p.spclust_wght; D.ww = h->p.spclust_wght * h->p.spclust_wght;
         D.sigma_shift = h->sigma;
@@ -929,48 +938,139 @@ static int run_impl(rhseg_handle *h)
         // ---- HSEG iterations, all sections at once ----
         int64_t max_iter = (int64_t)m0max + 2;
         int64_t it = 0;
-        while (true) {
-            const bool prof = h->p.profile != 0;
+        const bool prof = h->p.profile != 0;
+        // Two-group overlap (tensor-core screen, two sections or more): the
+        // sections s with s % 2 == g run on stream g, so that one group's
+        // step kernels (latency-bound, one block per section) run beside the
+        // other group's screen, which takes the narrow shape to leave room
+        // on every SM for a step block.  Within a chunk the second stream
+        // waits once, for the first group's first adjacent step; the two
+        // join at the chunk's end.
+        const int ngrp = (screen_uses_tcgen05(h->p.precision) && !inc && h->p.overlap && G.nsec >= 2 &&
+                          h->p.spclust_wght > 0.0) ? 2 : 1;
+        LevelDev DG[2] = {D, D};
+        int gridg[2] = {G.nsec, 0};
+        cudaStream_t sg[2] = {s, h->stream2};
+        if (ngrp == 2) {
+            for (int g = 0; g < 2; g++) {
+                DG[g].gnum = 2;
+                DG[g].gsel = g;
+                DG[g].tc_cfg = 1;
+                DG[g].wlist = h->wlist.p + (size_t)g * h->geo[L].nsec;
+                DG[g].wcount = h->wcount.p + g;
+                gridg[g] = (G.nsec - g + 1) / 2;
+            }
+        }
+        // one chunk of HSEG iterations, then the count of running sections and
+        // the device error word into pinned host memory
+        auto enqueue_chunk = [&]() -> int {
             for (int k = 0; k < chunk; k++) {
-                if (prof) CK(cudaEventRecord(h->prof_ev[(0 * chunk + k) * 2], s));
-                k_adj_step<<<G.nsec, STEP_THREADS, 0, s>>>(D, sc); h->nlaunch++;
-                if (prof) CK(cudaEventRecord(h->prof_ev[(0 * chunk + k) * 2 + 1], s));
-                if (h->p.spclust_wght > 0.0) {
-                    if (prof) CK(cudaEventRecord(h->prof_ev[(1 * chunk + k) * 2], s));
-                    if (inc) launch_srow_update(h, D);
-                    else launch_screen(h, D);
-                    if (prof) CK(cudaEventRecord(h->prof_ev[(1 * chunk + k) * 2 + 1], s));
-                    if (inc) k_spec_inc<<<G.nsec, STEP_THREADS, 0, s>>>(D, sc);
-                    else k_spec_step<<<G.nsec, STEP_THREADS, 0, s>>>(D, sc);
-                    h->nlaunch++;
-                    k_write_rows<<<h->n_sm * 4, 256, 0, s>>>(D, sc, 1); h->nlaunch++;
-                    if (prof) CK(cudaEventRecord(h->prof_ev[(2 * chunk + k) * 2 + 1], s));
+                for (int g = 0; g < ngrp; g++) {
+                    const LevelDev &Dg = DG[g];
+                    const cudaStream_t sq = sg[g];
+                    cudaEvent_t *pe = prof ? &h->prof_ev[(size_t)g * 3 * chunk * 2] : nullptr;
+                    // the second group starts once the first group's first
+                    // adjacent step is done: its steps then run beside the
+                    // first group's screen, and the two stay half a step apart
+                    if (g == 1 && k == 0) CK(cudaStreamWaitEvent(sq, h->ev_fork, 0));
+                    if (prof) CK(cudaEventRecord(pe[(0 * chunk + k) * 2], sq));
+                    k_adj_step<<<gridg[g], STEP_THREADS, 0, sq>>>(Dg, sc); h->nlaunch++;
+                    if (prof) CK(cudaEventRecord(pe[(0 * chunk + k) * 2 + 1], sq));
+                    if (ngrp == 2 && g == 0 && k == 0) CK(cudaEventRecord(h->ev_fork, sq));
+                    if (h->p.spclust_wght > 0.0) {
+                        if (prof) CK(cudaEventRecord(pe[(1 * chunk + k) * 2], sq));
+                        if (inc) launch_srow_update(h, Dg);
+                        else launch_screen(h, Dg, sq);
+                        if (prof) CK(cudaEventRecord(pe[(1 * chunk + k) * 2 + 1], sq));
+                        if (inc) k_spec_inc<<<gridg[g], STEP_THREADS, 0, sq>>>(Dg, sc);
+                        else k_spec_step<<<gridg[g], STEP_THREADS, 0, sq>>>(Dg, sc);
+                        h->nlaunch++;
+                        k_write_rows<<<h->n_sm * 4, 256, 0, sq>>>(Dg, sc, 1); h->nlaunch++;
+                        if (prof) CK(cudaEventRecord(pe[(2 * chunk + k) * 2 + 1], sq));
+                    }
                 }
+            }
+            if (ngrp == 2) {
+                CK(cudaEventRecord(h->ev_join, h->stream2));
+                CK(cudaStreamWaitEvent(s, h->ev_join, 0));
             }
             CK(cudaGetLastError());
             CK(h->launch_err);
-            it += chunk;
             k_count_active<<<1, 1024, 0, s>>>(h->st.p, G.nsec, h->active.p, h->err.p); h->nlaunch++;
             CK(cudaMemcpyAsync(h->active_host, h->active.p, 8, cudaMemcpyDeviceToHost, s));
-            CK(cudaStreamSynchronize(s));
+            return RHSEG_OK;
+        };
+        // Without per-kernel events the chunk is captured once per level as a
+        // CUDA graph (the kernels read all per-iteration state from the
+        // device, so every chunk of the level is the same graph) and replayed;
+        // the legacy default stream cannot be captured, so there the chunks
+        // are launched directly.
+        cudaGraphExec_t gexec = nullptr;
+        int64_t chunk_launches = 0, chunk_screens = 0;
+        if (!prof && !inc && s != nullptr && s != cudaStreamLegacy && s != cudaStreamPerThread) {
+            cudaGraph_t graph = nullptr;
+            const int64_t l0 = h->nlaunch, sc0 = h->nscreen;
+            if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+                const int rc_c = enqueue_chunk();
+                const cudaError_t ec = cudaStreamEndCapture(s, &graph);
+                if (rc_c == RHSEG_OK && ec == cudaSuccess && graph != nullptr &&
+                    cudaGraphInstantiate(&gexec, graph, 0) != cudaSuccess)
+                    gexec = nullptr;
+                if (graph) cudaGraphDestroy(graph);
+                if (rc_c != RHSEG_OK || ec != cudaSuccess) {
+                    if (gexec) cudaGraphExecDestroy(gexec);
+                    gexec = nullptr;
+                }
+            }
+            (void)cudaGetLastError();
+            h->launch_err = cudaSuccess;
+            chunk_launches = h->nlaunch - l0;
+            chunk_screens = h->nscreen - sc0;
+            h->nlaunch = l0;
+            h->nscreen = sc0;
+        }
+        while (true) {
+            if (gexec) {
+                const cudaError_t e = cudaGraphLaunch(gexec, s);
+                if (e != cudaSuccess) {
+                    cudaGraphExecDestroy(gexec);
+                    CK(e);
+                }
+                h->nlaunch += chunk_launches;
+                h->nscreen += chunk_screens;
+            } else {
+                int rcq = enqueue_chunk();
+                if (rcq) return rcq;
+            }
+            it += chunk;
+            {
+                const cudaError_t e = cudaStreamSynchronize(s);
+                if (e != cudaSuccess && gexec) cudaGraphExecDestroy(gexec);
+                CK(e);
+            }
             if (h->active_host[1]) {          // a device wait gave up or a check failed: stop here
                 int rc_err = err_word_code(h->active_host[1]);
                 snprintf(g_cuda_msg, sizeof(g_cuda_msg), "device error word 0x%08x at level %d", h->active_host[1], lev);
+                if (gexec) cudaGraphExecDestroy(gexec);
                 return rc_err;
             }
             if (prof) {
-                for (int k = 0; k < chunk; k++) {
-                    float a = 0, b = 0, c = 0;
-                    CK(cudaEventElapsedTime(&a, h->prof_ev[(0 * chunk + k) * 2], h->prof_ev[(0 * chunk + k) * 2 + 1]));
-                    h->stats.adj_ms += a;
-                    h->stats.level_adj_ms[lev - 1] += a;
-                    if (h->p.spclust_wght > 0.0) {
-                        CK(cudaEventElapsedTime(&b, h->prof_ev[(1 * chunk + k) * 2], h->prof_ev[(1 * chunk + k) * 2 + 1]));
-                        CK(cudaEventElapsedTime(&c, h->prof_ev[(1 * chunk + k) * 2 + 1], h->prof_ev[(2 * chunk + k) * 2 + 1]));
-                        h->stats.screen_ms += b;
-                        h->stats.spec_ms += c;
-                        h->stats.level_screen_ms[lev - 1] += b;
-                        h->stats.level_spec_ms[lev - 1] += c;
+                // summed over the launches of both groups (which overlap in time)
+                for (int g = 0; g < ngrp; g++) {
+                    const cudaEvent_t *pe = &h->prof_ev[(size_t)g * 3 * chunk * 2];
+                    for (int k = 0; k < chunk; k++) {
+                        float a = 0, b = 0, c = 0;
+                        CK(cudaEventElapsedTime(&a, pe[(0 * chunk + k) * 2], pe[(0 * chunk + k) * 2 + 1]));
+                        h->stats.adj_ms += a;
+                        h->stats.level_adj_ms[lev - 1] += a;
+                        if (h->p.spclust_wght > 0.0) {
+                            CK(cudaEventElapsedTime(&b, pe[(1 * chunk + k) * 2], pe[(1 * chunk + k) * 2 + 1]));
+                            CK(cudaEventElapsedTime(&c, pe[(1 * chunk + k) * 2 + 1], pe[(2 * chunk + k) * 2 + 1]));
+                            h->stats.screen_ms += b;
+                            h->stats.spec_ms += c;
+                            h->stats.level_screen_ms[lev - 1] += b;
+                            h->stats.level_spec_ms[lev - 1] += c;
+                        }
                     }
                 }
             }
@@ -978,9 +1078,11 @@ static int run_impl(rhseg_handle *h)
             if (it > max_iter + chunk) {
                 snprintf(g_cuda_msg, sizeof(g_cuda_msg), "level %d did not finish after %lld iterations", lev,
                          (long long)it);
+                if (gexec) cudaGraphExecDestroy(gexec);
                 return RHSEG_ETIMEOUT;
             }
         }
+        if (gexec) cudaGraphExecDestroy(gexec);
         CK(cudaMemcpyAsync(sth.data(), h->st.p, sizeof(SecState) * G.nsec, cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
         h->seglen[lev].resize(G.nsec);
@@ -1323,6 +1425,9 @@ extern "C" void rhseg_destroy(rhseg_handle *h)
     if (h->scan_host) cudaFreeHost(h->scan_host);
     h->scan_tmp.release();
     for (auto &e : h->prof_ev) cudaEventDestroy(e);
+    if (h->stream2) { cudaStreamSynchronize(h->stream2); cudaStreamDestroy(h->stream2); }
+    if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+    if (h->ev_join) cudaEventDestroy(h->ev_join);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
     delete h;
 }

@@ -447,7 +447,7 @@ __global__ void __launch_bounds__(STEP_THREADS) k_init_section(LevelDev L, Scree
 // HSEG step kernels
 // ---------------------------------------------------------------------------
 
-constexpr int PAIR_CAP = 1536;   // pair entries of one batched key phase
+constexpr int PAIR_CAP = 1408;   // pair entries of one batched key phase (static shared memory stays below 48 KB)
 constexpr int ROW_CAP = 256;     // rows whose best partner one merge recomputes (incl. the merged row)
 
 struct StepSmem {
@@ -712,7 +712,10 @@ __device__ void block_merge(const LevelDev &L, int sec, SecState &st, int a, int
             int r = w * 32 + __ffs(bits) - 1;
             bits &= bits - 1;
             int idx = atomicAdd(&sm.npair, 1);
-            if (idx < PAIR_CAP) { sm.pi[idx] = a; sm.pj[idx] = r; sm.prow[idx] = 0; }
+            if (idx < PAIR_CAP) {
+                sm.pi[idx] = a; sm.pj[idx] = r; sm.prow[idx] = 0;
+                prefetch_l2(L.S + (ro + r) * L.Bs, (uint32_t)(L.Bs * 8));
+            }
             else sm.overflow = 1;
         }
     }
@@ -739,7 +742,10 @@ __device__ void block_merge(const LevelDev &L, int sec, SecState &st, int a, int
                     int q = w * 32 + __ffs(bits) - 1;
                     bits &= bits - 1;
                     int idx = atomicAdd(&sm.npair, 1);
-                    if (idx < PAIR_CAP) { sm.pi[idx] = r; sm.pj[idx] = q; sm.prow[idx] = (int16_t)k; }
+                    if (idx < PAIR_CAP) {
+                        sm.pi[idx] = r; sm.pj[idx] = q; sm.prow[idx] = (int16_t)k;
+                        prefetch_l2(L.S + (ro + q) * L.Bs, (uint32_t)(L.Bs * 8));
+                    }
                     else sm.overflow = 1;
                 }
             }
@@ -1221,10 +1227,10 @@ __global__ void __launch_bounds__(STEP_THREADS) k_sort_positions(LevelDev L)
 // Step 2 of HSEG: merge the adjacent pair of minimum key.
 __global__ void __launch_bounds__(STEP_THREADS, 2) k_adj_step(LevelDev L, ScreenConst sc)
 {
-    const int sec = blockIdx.x;
+    const int sec = step_section(L);
     // a new iteration: the list of sections whose rows are to be rewritten
     // starts empty (the previous iteration's k_write_rows has finished)
-    if (sec == 0 && threadIdx.x == 0 && L.wcount != nullptr) *L.wcount = 0;
+    if (blockIdx.x == 0 && threadIdx.x == 0 && L.wcount != nullptr) *L.wcount = 0;
     if (sec >= L.nsec) return;
     __shared__ StepSmem sm;
     if (threadIdx.x == 0) sm.st = L.st[sec];
@@ -1378,7 +1384,7 @@ __device__ void block_screen_error(const LevelDev &L, int sec, SecState &st, con
 // enough regions died, a new compact position list for the screen.
 __global__ void __launch_bounds__(STEP_THREADS, 2) k_spec_step(LevelDev L, ScreenConst sc)
 {
-    const int sec = blockIdx.x;
+    const int sec = step_section(L);
     if (sec >= L.nsec) return;
     __shared__ StepSmem sm;
     if (threadIdx.x == 0) sm.st = L.st[sec];
@@ -1422,6 +1428,8 @@ __global__ void __launch_bounds__(STEP_THREADS, 2) k_spec_step(LevelDev L, Scree
                     const int idx = atomicAdd(&sm.npair, 1);
                     sm.pi[idx] = min(i, j);
                     sm.pj[idx] = max(i, j);
+                    prefetch_l2(L.S + (ro + i) * L.Bs, (uint32_t)(L.Bs * 8));
+                    prefetch_l2(L.S + (ro + j) * L.Bs, (uint32_t)(L.Bs * 8));
                     sm.prow[idx] = (int16_t)(c - c0);       // the entry's candidate
                 }
                 __syncthreads();
