@@ -303,14 +303,6 @@ __device__ __forceinline__ double warp_key(const int64_t *__restrict__ Si, int64
 
 __device__ __forceinline__ uint64_t dbits(double x) { return (uint64_t)__double_as_longlong(x); }
 
-// Bring `bytes` (a multiple of 16, from a 16-byte aligned address) into L2
-// ahead of their use: a hint, with no register or completion to wait for.
-// The region rows whose exact keys a step needs are found a few dependent
-// reads before the keys are computed; prefetched then, the key loads hit L2.
-__device__ __forceinline__ void prefetch_l2(const void *p, uint32_t bytes)
-{
-    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
-}
 
 // Packed (K bits, lo slot, hi slot) comparisons.
 // Decode a local upper-triangle tile index into (I, J), I <= J < nb

@@ -712,10 +712,7 @@ __device__ void block_merge(const LevelDev &L, int sec, SecState &st, int a, int
             int r = w * 32 + __ffs(bits) - 1;
             bits &= bits - 1;
             int idx = atomicAdd(&sm.npair, 1);
-            if (idx < PAIR_CAP) {
-                sm.pi[idx] = a; sm.pj[idx] = r; sm.prow[idx] = 0;
-                prefetch_l2(L.S + (ro + r) * L.Bs, (uint32_t)(L.Bs * 8));
-            }
+            if (idx < PAIR_CAP) { sm.pi[idx] = a; sm.pj[idx] = r; sm.prow[idx] = 0; }
             else sm.overflow = 1;
         }
     }
@@ -742,10 +739,7 @@ __device__ void block_merge(const LevelDev &L, int sec, SecState &st, int a, int
                     int q = w * 32 + __ffs(bits) - 1;
                     bits &= bits - 1;
                     int idx = atomicAdd(&sm.npair, 1);
-                    if (idx < PAIR_CAP) {
-                        sm.pi[idx] = r; sm.pj[idx] = q; sm.prow[idx] = (int16_t)k;
-                        prefetch_l2(L.S + (ro + q) * L.Bs, (uint32_t)(L.Bs * 8));
-                    }
+                    if (idx < PAIR_CAP) { sm.pi[idx] = r; sm.pj[idx] = q; sm.prow[idx] = (int16_t)k; }
                     else sm.overflow = 1;
                 }
             }
@@ -1428,8 +1422,6 @@ __global__ void __launch_bounds__(STEP_THREADS, 2) k_spec_step(LevelDev L, Scree
                     const int idx = atomicAdd(&sm.npair, 1);
                     sm.pi[idx] = min(i, j);
                     sm.pj[idx] = max(i, j);
-                    prefetch_l2(L.S + (ro + i) * L.Bs, (uint32_t)(L.Bs * 8));
-                    prefetch_l2(L.S + (ro + j) * L.Bs, (uint32_t)(L.Bs * 8));
                     sm.prow[idx] = (int16_t)(c - c0);       // the entry's candidate
                 }
                 __syncthreads();

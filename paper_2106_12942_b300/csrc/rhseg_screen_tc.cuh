@@ -54,6 +54,7 @@ constexpr int TC_THREADS = 32 * (TC_PROD_WARPS + 1 + TC_EPI_WARPS);
 static_assert(TC_STAGES % TC_PROD_WARPS == 0, "each producer owns whole ring slots");
 constexpr uint32_t TC_TMEM_COLS = 2 * TC_N;
 constexpr long long TC_WAIT_CYCLES = 4000000000ll;           // default wait bound: about 2 s at 2 GHz
+constexpr int TC_UCACHE = 512;                // units per CTA decoded in the prologue (the rest on the way)
 
 // One work unit: rows [rowA, rowA + 128) against rows [rowB, rowB + 256).
 struct TcUnit {
@@ -76,6 +77,8 @@ struct TcShared {
     long long pre[MAX_SECTIONS + 1];
     int smc[MAX_SECTIONS];                    // per section: positions this step
     int spoff[MAX_SECTIONS];                  // per section: first operand row
+    int usec[TC_UCACHE];                      // this CTA's first TC_UCACHE units: section
+    int uent[TC_UCACHE];                      //   and (I << 16) | Jp, read in one pass at the start
 };
 __host__ __device__ constexpr int tc_smem_bytes(int nstage)
 {
@@ -374,6 +377,17 @@ __device__ __forceinline__ bool tc_unit(const TcShared &sh, const TcJob &job, lo
     return true;
 }
 
+// Unit k of this CTA from the prologue's cache (k < TC_UCACHE, screen mode).
+__device__ __forceinline__ void tc_unit_cached(const TcShared &sh, long long k, TcUnit &u)
+{
+    const int s = sh.usec[k], e = sh.uent[k];
+    u.sec = s;
+    u.I = e >> 16;
+    u.Jp = e & 0xffff;
+    u.rowA = sh.spoff[s] + (int64_t)u.I * TC_TILE;
+    u.rowB = sh.spoff[s] + (int64_t)u.Jp * TC_N;
+}
+
 template <int FMT, int NPROD, int NSTAGE, int NEPI>
 __global__ void __launch_bounds__(32 * (NPROD + 1 + NEPI), (32 * (NPROD + 1 + NEPI) <= 256) ? 2 : 1)
     k_screen_tc(LevelDev L, const __grid_constant__ CUtensorMap tmap, TcJob job)
@@ -406,6 +420,17 @@ __global__ void __launch_bounds__(32 * (NPROD + 1 + NEPI), (32 * (NPROD + 1 + NE
             sh.spoff[s] = (int)L.poff[s];
         }
         cursor0 = find_section(sh.pre, L.nsec, blockIdx.x);
+        // this CTA's units, all loaded together: the producers then decode
+        // them without a dependent global read per unit
+        if (L.ulist != nullptr) {
+            const long long nc = my_units < TC_UCACHE ? my_units : TC_UCACHE;
+            for (long long k = threadIdx.x; k < nc; k += blockDim.x) {
+                const long long t = blockIdx.x + k * gridDim.x;
+                const int sc = find_section(sh.pre, L.nsec, t);
+                sh.usec[k] = sc;
+                sh.uent[k] = L.ulist[(int64_t)sc * L.ucap + (t - sh.pre[sc])];
+            }
+        }
     }
 
     // K slices per commit: TC_GROUP (or the tuned L.tc_group, at most the ring), widened for very wide rows so that a
@@ -459,8 +484,11 @@ __global__ void __launch_bounds__(32 * (NPROD + 1 + NEPI), (32 * (NPROD + 1 + NE
                 const int kc = (int)(c - k * natoms);
                 const int slot = (int)(c % NSTAGE);
                 if (k != kdec) {
-                    tc_unit(sh, job, blockIdx.x + k * gridDim.x, total, cursor, u, job.gram_rows > 0 ? nullptr : L.ulist,
-                            L.ucap);
+                    if (job.gram_rows == 0 && L.ulist != nullptr && k < TC_UCACHE)
+                        tc_unit_cached(sh, k, u);
+                    else
+                        tc_unit(sh, job, blockIdx.x + k * gridDim.x, total, cursor, u,
+                                job.gram_rows > 0 ? nullptr : L.ulist, L.ucap);
                     kdec = k;
                 }
                 if (kc == 0) {
