@@ -212,8 +212,6 @@ def main():
     ap.add_argument("--autotune", type=int, default=1, choices=[0, 1],
                     help="1: the screen schedule the autotuner stored for this band count and section size "
                          "(paper_2106_12942_b300/autotune_cache.json), if any")
-    ap.add_argument("--overlap", type=int, default=0, choices=[0, 1],
-                    help="1: the even and odd sections of a level on two overlapping streams")
     ap.add_argument("--profile", type=int, default=1, choices=[0, 1],
                     help="1: CUDA events around every step kernel (per-kernel times, the roofline's launch "
                          "times); 0: none, the run as a user makes it")
@@ -243,7 +241,6 @@ def main():
     if args.multi_merge is not None:
         params["multi_merge"] = args.multi_merge
     params["profile"] = args.profile
-    params["overlap"] = args.overlap
     tuned = {}
     if args.autotune and params.get("precision") in (1, 2):
         from paper_2106_12942_b300 import autotune

@@ -106,11 +106,7 @@ typedef struct rhseg_params {
     int32_t screen_group;  /* tensor-core screen: K slices (32 bands each) whose MMAs
                               share one tcgen05.commit, 1..8, 0 = the default (4); a
                               tile-shape choice of the autotuner (results identical) */
-    int32_t overlap;       /* 1: with the tensor-core screen and two sections or more,
-                              the even and odd sections of a level run on two streams,
-                              so that one group's step kernels can run beside the other
-                              group's screen (which then takes a narrower shape); 0
-                              (default): every section in one stream.  Results identical */
+    int32_t reserved;      /* set to 0 */
 } rhseg_params;
 
 /* One merge-log record.  kind 0 = adjacent merge, 1 = spectral merge,

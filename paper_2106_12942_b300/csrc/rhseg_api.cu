@@ -198,9 +198,7 @@ struct rhseg_handle {
     DBuf<rhseg_merge> log_out;
     // instrumentation
     int64_t nlaunch = 0, nscreen = 0;
-    std::vector<cudaEvent_t> prof_ev;   // [group][3 kernels][chunk][2]
-    cudaStream_t stream2 = nullptr;     // second group's stream (two-group overlap)
-    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    std::vector<cudaEvent_t> prof_ev;   // [3 kernels][chunk][2]
     CUtensorMap tmap;                   // operand rows of the tensor-core screen
     cudaError_t launch_err = cudaSuccess;
 };
@@ -220,7 +218,6 @@ static int check_params(const rhseg_params *p, int32_t rows, int32_t cols, int32
     if (p->multi_merge && p->incremental) return RHSEG_EINVAL;
     if (p->wait_cycles < 0) return RHSEG_EINVAL;
     if (p->screen_group < 0 || p->screen_group > 8) return RHSEG_EINVAL;
-    if (p->overlap < 0 || p->overlap > 1) return RHSEG_EINVAL;
     return RHSEG_OK;
 }
 
@@ -491,12 +488,9 @@ static int common_create(rhseg_handle *h, const rhseg_params *p, void *stream)
     if ((rc = h->ref.alloc((size_t)nsec_max * h->Bs))) return rc;
     if ((rc = h->log.alloc(h->log_cap))) return rc;
     if ((rc = h->err.alloc(1))) return rc;
-    if ((rc = h->wlist.alloc(2 * (size_t)nsec_max))) return rc;
-    if ((rc = h->wcount.alloc(2))) return rc;
-    CK(cudaMemset(h->wcount.p, 0, 8));
-    CK(cudaStreamCreateWithFlags(&h->stream2, cudaStreamNonBlocking));
-    CK(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
-    CK(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
+    if ((rc = h->wlist.alloc(nsec_max))) return rc;
+    if ((rc = h->wcount.alloc(1))) return rc;
+    CK(cudaMemset(h->wcount.p, 0, 4));
     if ((rc = h->active.alloc(2))) return rc;
     CK(cudaMallocHost((void **)&h->active_host, 2 * sizeof(int32_t)));
     CK(cudaMallocHost((void **)&h->scan_host, 2 * sizeof(unsigned long long)));
@@ -755,7 +749,7 @@ static int run_impl(rhseg_handle *h)
     h->nscreen = 0;
     const int chunk = 32;
     if (h->p.profile && h->prof_ev.empty()) {
-        h->prof_ev.resize(2 * 3 * chunk * 2);
+        h->prof_ev.resize(3 * chunk * 2);
         for (auto &e : h->prof_ev) CK(cudaEventCreate(&e));
     }
     h->seglen.assign(L + 1, {});
@@ -939,60 +933,24 @@ static int run_impl(rhseg_handle *h)
         int64_t max_iter = (int64_t)m0max + 2;
         int64_t it = 0;
         const bool prof = h->p.profile != 0;
-        // Two-group overlap (tensor-core screen, two sections or more): the
-        // sections s with s % 2 == g run on stream g, so that one group's
-        // step kernels (latency-bound, one block per section) run beside the
-        // other group's screen, which takes the narrow shape to leave room
-        // on every SM for a step block.  Within a chunk the second stream
-        // waits once, for the first group's first adjacent step; the two
-        // join at the chunk's end.
-        const int ngrp = (screen_uses_tcgen05(h->p.precision) && !inc && h->p.overlap && G.nsec >= 2 &&
-                          h->p.spclust_wght > 0.0) ? 2 : 1;
-        LevelDev DG[2] = {D, D};
-        int gridg[2] = {G.nsec, 0};
-        cudaStream_t sg[2] = {s, h->stream2};
-        if (ngrp == 2) {
-            for (int g = 0; g < 2; g++) {
-                DG[g].gnum = 2;
-                DG[g].gsel = g;
-                DG[g].tc_cfg = 1;
-                DG[g].wlist = h->wlist.p + (size_t)g * h->geo[L].nsec;
-                DG[g].wcount = h->wcount.p + g;
-                gridg[g] = (G.nsec - g + 1) / 2;
-            }
-        }
         // one chunk of HSEG iterations, then the count of running sections and
         // the device error word into pinned host memory
         auto enqueue_chunk = [&]() -> int {
             for (int k = 0; k < chunk; k++) {
-                for (int g = 0; g < ngrp; g++) {
-                    const LevelDev &Dg = DG[g];
-                    const cudaStream_t sq = sg[g];
-                    cudaEvent_t *pe = prof ? &h->prof_ev[(size_t)g * 3 * chunk * 2] : nullptr;
-                    // the second group starts once the first group's first
-                    // adjacent step is done: its steps then run beside the
-                    // first group's screen, and the two stay half a step apart
-                    if (g == 1 && k == 0) CK(cudaStreamWaitEvent(sq, h->ev_fork, 0));
-                    if (prof) CK(cudaEventRecord(pe[(0 * chunk + k) * 2], sq));
-                    k_adj_step<<<gridg[g], STEP_THREADS, 0, sq>>>(Dg, sc); h->nlaunch++;
-                    if (prof) CK(cudaEventRecord(pe[(0 * chunk + k) * 2 + 1], sq));
-                    if (ngrp == 2 && g == 0 && k == 0) CK(cudaEventRecord(h->ev_fork, sq));
-                    if (h->p.spclust_wght > 0.0) {
-                        if (prof) CK(cudaEventRecord(pe[(1 * chunk + k) * 2], sq));
-                        if (inc) launch_srow_update(h, Dg);
-                        else launch_screen(h, Dg, sq);
-                        if (prof) CK(cudaEventRecord(pe[(1 * chunk + k) * 2 + 1], sq));
-                        if (inc) k_spec_inc<<<gridg[g], STEP_THREADS, 0, sq>>>(Dg, sc);
-                        else k_spec_step<<<gridg[g], STEP_THREADS, 0, sq>>>(Dg, sc);
-                        h->nlaunch++;
-                        k_write_rows<<<h->n_sm * 4, 256, 0, sq>>>(Dg, sc, 1); h->nlaunch++;
-                        if (prof) CK(cudaEventRecord(pe[(2 * chunk + k) * 2 + 1], sq));
-                    }
+                if (prof) CK(cudaEventRecord(h->prof_ev[(0 * chunk + k) * 2], s));
+                k_adj_step<<<G.nsec, STEP_THREADS, 0, s>>>(D, sc); h->nlaunch++;
+                if (prof) CK(cudaEventRecord(h->prof_ev[(0 * chunk + k) * 2 + 1], s));
+                if (h->p.spclust_wght > 0.0) {
+                    if (prof) CK(cudaEventRecord(h->prof_ev[(1 * chunk + k) * 2], s));
+                    if (inc) launch_srow_update(h, D);
+                    else launch_screen(h, D, s);
+                    if (prof) CK(cudaEventRecord(h->prof_ev[(1 * chunk + k) * 2 + 1], s));
+                    if (inc) k_spec_inc<<<G.nsec, STEP_THREADS, 0, s>>>(D, sc);
+                    else k_spec_step<<<G.nsec, STEP_THREADS, 0, s>>>(D, sc);
+                    h->nlaunch++;
+                    k_write_rows<<<h->n_sm * 4, 256, 0, s>>>(D, sc, 1); h->nlaunch++;
+                    if (prof) CK(cudaEventRecord(h->prof_ev[(2 * chunk + k) * 2 + 1], s));
                 }
-            }
-            if (ngrp == 2) {
-                CK(cudaEventRecord(h->ev_join, h->stream2));
-                CK(cudaStreamWaitEvent(s, h->ev_join, 0));
             }
             CK(cudaGetLastError());
             CK(h->launch_err);
@@ -1055,22 +1013,18 @@ static int run_impl(rhseg_handle *h)
                 return rc_err;
             }
             if (prof) {
-                // summed over the launches of both groups (which overlap in time)
-                for (int g = 0; g < ngrp; g++) {
-                    const cudaEvent_t *pe = &h->prof_ev[(size_t)g * 3 * chunk * 2];
-                    for (int k = 0; k < chunk; k++) {
-                        float a = 0, b = 0, c = 0;
-                        CK(cudaEventElapsedTime(&a, pe[(0 * chunk + k) * 2], pe[(0 * chunk + k) * 2 + 1]));
-                        h->stats.adj_ms += a;
-                        h->stats.level_adj_ms[lev - 1] += a;
-                        if (h->p.spclust_wght > 0.0) {
-                            CK(cudaEventElapsedTime(&b, pe[(1 * chunk + k) * 2], pe[(1 * chunk + k) * 2 + 1]));
-                            CK(cudaEventElapsedTime(&c, pe[(1 * chunk + k) * 2 + 1], pe[(2 * chunk + k) * 2 + 1]));
-                            h->stats.screen_ms += b;
-                            h->stats.spec_ms += c;
-                            h->stats.level_screen_ms[lev - 1] += b;
-                            h->stats.level_spec_ms[lev - 1] += c;
-                        }
+                for (int k = 0; k < chunk; k++) {
+                    float a = 0, b = 0, c = 0;
+                    CK(cudaEventElapsedTime(&a, h->prof_ev[(0 * chunk + k) * 2], h->prof_ev[(0 * chunk + k) * 2 + 1]));
+                    h->stats.adj_ms += a;
+                    h->stats.level_adj_ms[lev - 1] += a;
+                    if (h->p.spclust_wght > 0.0) {
+                        CK(cudaEventElapsedTime(&b, h->prof_ev[(1 * chunk + k) * 2], h->prof_ev[(1 * chunk + k) * 2 + 1]));
+                        CK(cudaEventElapsedTime(&c, h->prof_ev[(1 * chunk + k) * 2 + 1], h->prof_ev[(2 * chunk + k) * 2 + 1]));
+                        h->stats.screen_ms += b;
+                        h->stats.spec_ms += c;
+                        h->stats.level_screen_ms[lev - 1] += b;
+                        h->stats.level_spec_ms[lev - 1] += c;
                     }
                 }
             }
@@ -1425,9 +1379,6 @@ extern "C" void rhseg_destroy(rhseg_handle *h)
     if (h->scan_host) cudaFreeHost(h->scan_host);
     h->scan_tmp.release();
     for (auto &e : h->prof_ev) cudaEventDestroy(e);
-    if (h->stream2) { cudaStreamSynchronize(h->stream2); cudaStreamDestroy(h->stream2); }
-    if (h->ev_fork) cudaEventDestroy(h->ev_fork);
-    if (h->ev_join) cudaEventDestroy(h->ev_join);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
     delete h;
 }

@@ -95,10 +95,6 @@ struct LevelDev {
     int32_t *err;              // device error word
     long long wait_cycles;     // bound of the screen's pipeline waits (0: the default)
     int32_t tc_group;          // K slices per tcgen05.commit of the screen (0: the default)
-    int32_t tc_cfg;            // screen shape: 0 wide (the SM to itself), 1 narrow (a step block beside it)
-    // two-group overlap: the per-iteration kernels of this launch cover the
-    // sections s with s % gnum == gsel (gnum <= 1: every section)
-    int32_t gnum, gsel;
     int32_t *wlist;            // [nsec] sections whose positions were rebuilt this iteration
     int32_t *wcount;           // their number
     // incremental spectral minima (null unless that mode is on)
@@ -128,19 +124,6 @@ struct LevelDev {
     uint64_t *mK;              // per slot: K bits of the best below-threshold non-adjacent pair
     uint32_t *mP;              // per slot: partner slot of that pair (~0u: none)
 };
-
-// Section of this block in a per-iteration step kernel (one block per
-// section of the launch's group).
-__device__ __forceinline__ int step_section(const LevelDev &L)
-{
-    return L.gnum > 1 ? (int)blockIdx.x * L.gnum + L.gsel : (int)blockIdx.x;
-}
-
-// The section belongs to this launch's group.
-__device__ __forceinline__ bool in_group(const LevelDev &L, int s)
-{
-    return L.gnum <= 1 || s % L.gnum == L.gsel;
-}
 
 // ---------------------------------------------------------------------------
 // Exact 128-bit helpers

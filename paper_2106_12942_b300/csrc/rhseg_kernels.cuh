@@ -1221,7 +1221,7 @@ __global__ void __launch_bounds__(STEP_THREADS) k_sort_positions(LevelDev L)
 // Step 2 of HSEG: merge the adjacent pair of minimum key.
 __global__ void __launch_bounds__(STEP_THREADS, 2) k_adj_step(LevelDev L, ScreenConst sc)
 {
-    const int sec = step_section(L);
+    const int sec = blockIdx.x;
     // a new iteration: the list of sections whose rows are to be rewritten
     // starts empty (the previous iteration's k_write_rows has finished)
     if (blockIdx.x == 0 && threadIdx.x == 0 && L.wcount != nullptr) *L.wcount = 0;
@@ -1378,7 +1378,7 @@ __device__ void block_screen_error(const LevelDev &L, int sec, SecState &st, con
 // enough regions died, a new compact position list for the screen.
 __global__ void __launch_bounds__(STEP_THREADS, 2) k_spec_step(LevelDev L, ScreenConst sc)
 {
-    const int sec = step_section(L);
+    const int sec = blockIdx.x;
     if (sec >= L.nsec) return;
     __shared__ StepSmem sm;
     if (threadIdx.x == 0) sm.st = L.st[sec];

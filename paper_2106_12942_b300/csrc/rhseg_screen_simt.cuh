@@ -43,7 +43,7 @@ __device__ void block_tile_prefix(const LevelDev &L, int tile, long long *pre)
     for (int k = 0; k < 16; k++) {
         int s = s0 + k;
         long long t = 0;
-        if (k < per && s < nsec && in_group(L, s)) {
+        if (k < per && s < nsec) {
             const SecState &st = L.st[s];
             if (tile < 0) {
                 if (!st.done) {

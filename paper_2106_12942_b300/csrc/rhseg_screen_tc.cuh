@@ -54,7 +54,6 @@ constexpr int TC_THREADS = 32 * (TC_PROD_WARPS + 1 + TC_EPI_WARPS);
 static_assert(TC_STAGES % TC_PROD_WARPS == 0, "each producer owns whole ring slots");
 constexpr uint32_t TC_TMEM_COLS = 2 * TC_N;
 constexpr long long TC_WAIT_CYCLES = 4000000000ll;           // default wait bound: about 2 s at 2 GHz
-constexpr int TC_UCACHE = 512;                // units per CTA decoded in the prologue (the rest on the way)
 
 // One work unit: rows [rowA, rowA + 128) against rows [rowB, rowB + 256).
 struct TcUnit {
@@ -77,41 +76,23 @@ struct TcShared {
     long long pre[MAX_SECTIONS + 1];
     int smc[MAX_SECTIONS];                    // per section: positions this step
     int spoff[MAX_SECTIONS];                  // per section: first operand row
-    int usec[TC_UCACHE];                      // this CTA's first TC_UCACHE units: section
-    int uent[TC_UCACHE];                      //   and (I << 16) | Jp, read in one pass at the start
 };
-__host__ __device__ constexpr int tc_smem_bytes(int nstage)
-{
-    return nstage * TC_STAGE_BYTES + 1024 + (int)((sizeof(TcShared) + 127) / 128 * 128);
-}
-constexpr int TC_SMEM_BYTES = tc_smem_bytes(TC_STAGES);
+constexpr int TC_SMEM_BYTES = TC_STAGES * TC_STAGE_BYTES + 1024 + (int)((sizeof(TcShared) + 127) / 128 * 128);
 static_assert(TC_SMEM_BYTES <= 227 * 1024, "screen shared memory");
 static_assert(TC_SMEM_BYTES > 227 * 1024 / 2, "one CTA per SM: the tensor memory is allocated whole");
 
-// The screen's two shapes.  Wide (0): 4 producer warps, an 8-slot ring and
-// 8 epilogue warps, the whole SM to itself.  Narrow (1): 3 producer warps, a
-// 6-slot ring and 4 epilogue warps, 256 threads of at most 128 registers and
-// about 168 KB of shared memory, so that a step-kernel block (256 threads,
-// 48 KB) fits on the same SM and runs beside it.
-constexpr int TC_N_PROD = 3, TC_N_STAGE = 6, TC_N_EPI = 4;
-constexpr int TC_N_THREADS = 32 * (TC_N_PROD + 1 + TC_N_EPI);
-constexpr int TC_N_SMEM_BYTES = tc_smem_bytes(TC_N_STAGE);
-static_assert(TC_N_SMEM_BYTES + 1024 + 48 * 1024 + 1024 <= 228 * 1024, "a step block fits beside the narrow screen");
-static_assert(TC_N_SMEM_BYTES > 227 * 1024 / 2, "one screen CTA per SM: the tensor memory is allocated whole");
-
 // Barrier 1 over the epilogue threads with an OR-reduction of `v`: every
 // participant gets the same answer.
-template <int NT>
 __device__ __forceinline__ bool epi_bar_or(bool v)
 {
     uint32_t out;
     asm volatile(
         "{\n\t.reg .pred q, p;\n\t"
         "setp.ne.u32 q, %1, 0;\n\t"
-        "bar.red.or.pred p, 1, %2, q;\n\t"
+        "bar.red.or.pred p, 1, 256, q;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}"
         : "=r"(out)
-        : "r"((uint32_t)v), "n"(NT)
+        : "r"((uint32_t)v)
         : "memory");
     return out != 0;
 }
@@ -377,29 +358,13 @@ __device__ __forceinline__ bool tc_unit(const TcShared &sh, const TcJob &job, lo
     return true;
 }
 
-// Unit k of this CTA from the prologue's cache (k < TC_UCACHE, screen mode).
-__device__ __forceinline__ void tc_unit_cached(const TcShared &sh, long long k, TcUnit &u)
+template <int FMT>
+__global__ void __launch_bounds__(TC_THREADS, 1) k_screen_tc(LevelDev L, const __grid_constant__ CUtensorMap tmap,
+                                                             TcJob job)
 {
-    const int s = sh.usec[k], e = sh.uent[k];
-    u.sec = s;
-    u.I = e >> 16;
-    u.Jp = e & 0xffff;
-    u.rowA = sh.spoff[s] + (int64_t)u.I * TC_TILE;
-    u.rowB = sh.spoff[s] + (int64_t)u.Jp * TC_N;
-}
-
-template <int FMT, int NPROD, int NSTAGE, int NEPI>
-__global__ void __launch_bounds__(32 * (NPROD + 1 + NEPI), (32 * (NPROD + 1 + NEPI) <= 256) ? 2 : 1)
-    k_screen_tc(LevelDev L, const __grid_constant__ CUtensorMap tmap, TcJob job)
-{
-    static_assert(NSTAGE % NPROD == 0 && NSTAGE <= TC_STAGES, "each producer owns whole ring slots");
-    static_assert(NEPI == 4 || NEPI == 8, "the epilogue covers the 4 lane quarters once or twice");
-    constexpr int P_MMA = NPROD;                    // MMA warp
-    constexpr int P_EPI0 = NPROD + 1;               // first epilogue warp
-    constexpr int NCH = (NEPI == 8) ? 1 : 2;        // 128-column halves per epilogue thread
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t *ring = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    TcShared &sh = *(TcShared *)(ring + NSTAGE * TC_STAGE_BYTES);
+    TcShared &sh = *(TcShared *)(ring + TC_STAGES * TC_STAGE_BYTES);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int natoms = L.Bpad / TC_KATOM;                       // K slices (pipeline stages) per unit
     const long long wc = L.wait_cycles > 0 ? L.wait_cycles : TC_WAIT_CYCLES;   // bound of every pipeline wait
@@ -420,40 +385,30 @@ __global__ void __launch_bounds__(32 * (NPROD + 1 + NEPI), (32 * (NPROD + 1 + NE
             sh.spoff[s] = (int)L.poff[s];
         }
         cursor0 = find_section(sh.pre, L.nsec, blockIdx.x);
-        // this CTA's units, all loaded together: the producers then decode
-        // them without a dependent global read per unit
-        if (L.ulist != nullptr) {
-            const long long nc = my_units < TC_UCACHE ? my_units : TC_UCACHE;
-            for (long long k = threadIdx.x; k < nc; k += blockDim.x) {
-                const long long t = blockIdx.x + k * gridDim.x;
-                const int sc = find_section(sh.pre, L.nsec, t);
-                sh.usec[k] = sc;
-                sh.uent[k] = L.ulist[(int64_t)sc * L.ucap + (t - sh.pre[sc])];
-            }
-        }
     }
 
-    // K slices per commit: TC_GROUP (or the tuned L.tc_group, at most the ring), widened for very wide rows so that a
+    // K slices per commit: the tuned L.tc_group (0: TC_GROUP), at most the
+    // ring's depth, and widened for very wide rows so that a
     // unit never spans more than 16 groups (the group barriers are reused
     // after TC_NGBAR groups; the epilogue trails the MMAs by at most one unit)
-    const int G = max(min(L.tc_group > 0 ? L.tc_group : TC_GROUP, NSTAGE), (natoms + 15) / 16);
+    const int G = max(min(L.tc_group > 0 ? L.tc_group : TC_GROUP, TC_STAGES), (natoms + 15) / 16);
     const int gpu = (natoms + G - 1) / G;                    // groups per unit
-    if (G > NSTAGE) {                 // a group must fit the ring (rows of at most 4096 elements)
+    if (G > TC_STAGES) {                 // a group must fit the ring (rows of at most 4096 elements)
         if (threadIdx.x == 0 && L.err) atomicExch(L.err, 0x54434752);
         return;                          // uniform: before any barrier or tensor-memory use
     }
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < NSTAGE; s++) { mbar_init(&sh.full[s], 1); sh.slot_q[s] = -1; sh.slot_fills[s] = 0; }
+        for (int s = 0; s < TC_STAGES; s++) { mbar_init(&sh.full[s], 1); sh.slot_q[s] = -1; sh.slot_fills[s] = 0; }
         for (int g = 0; g < TC_NGBAR; g++) mbar_init(&sh.gbar[g], 1);
-        for (int b = 0; b < 2; b++) mbar_init(&sh.tempty[b], NEPI);
-        for (int d = 0; d < TC_NDESC; d++) { mbar_init(&sh.dfull[d], 1); mbar_init(&sh.dempty[d], NEPI); }
+        for (int b = 0; b < 2; b++) mbar_init(&sh.tempty[b], TC_EPI_WARPS);
+        for (int d = 0; d < TC_NDESC; d++) { mbar_init(&sh.dfull[d], 1); mbar_init(&sh.dempty[d], TC_EPI_WARPS); }
         mbar_init(&sh.drain, 1);
         sh.abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
-    if (warp == P_MMA) {
+    if (warp == TC_MMA_WARP) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&sh.tmem_base)),
                      "r"(TC_TMEM_COLS)
                      : "memory");
@@ -465,10 +420,10 @@ __global__ void __launch_bounds__(32 * (NPROD + 1 + NEPI), (32 * (NPROD + 1 + NE
     const uint32_t tbase = sh.tmem_base;
     volatile int *abort = &sh.abort;
 
-    if (warp < NPROD) {
+    if (warp < TC_PROD_WARPS) {
         // ---------------- producers: unit decode + TMA ----------------
-        // Producer p streams the K slices c = p, p + NPROD, ... of this CTA's
-        // sequence (slot c mod NSTAGE, so each producer owns whole ring slots); the
+        // Producer p streams the K slices c = p, p + 4, ... of this CTA's
+        // sequence (slot c mod 8, so each producer owns two ring slots); the
         // producer of a unit's first slice publishes the unit's descriptor
         // for the epilogue.  A slot is refilled once the commit group that
         // read it has completed.
@@ -479,16 +434,13 @@ __global__ void __launch_bounds__(32 * (NPROD + 1 + NEPI), (32 * (NPROD + 1 + NE
             long long kdec = -1;
             TcUnit u{};
             const long long nslices = my_units * natoms;
-            for (long long c = p; c < nslices && !*abort; c += NPROD) {
+            for (long long c = p; c < nslices && !*abort; c += TC_PROD_WARPS) {
                 const long long k = c / natoms;
                 const int kc = (int)(c - k * natoms);
-                const int slot = (int)(c % NSTAGE);
+                const int slot = (int)(c % TC_STAGES);
                 if (k != kdec) {
-                    if (job.gram_rows == 0 && L.ulist != nullptr && k < TC_UCACHE)
-                        tc_unit_cached(sh, k, u);
-                    else
-                        tc_unit(sh, job, blockIdx.x + k * gridDim.x, total, cursor, u,
-                                job.gram_rows > 0 ? nullptr : L.ulist, L.ucap);
+                    tc_unit(sh, job, blockIdx.x + k * gridDim.x, total, cursor, u, job.gram_rows > 0 ? nullptr : L.ulist,
+                            L.ucap);
                     kdec = k;
                 }
                 if (kc == 0) {
@@ -512,11 +464,11 @@ __global__ void __launch_bounds__(32 * (NPROD + 1 + NEPI), (32 * (NPROD + 1 + NE
             }
             // every load this producer issued has landed before the CTA may
             // exit (immediate unless the CTA aborted with copies in flight)
-            for (int sl = p; sl < NSTAGE; sl += NPROD)
+            for (int sl = p; sl < TC_STAGES; sl += TC_PROD_WARPS)
                 if (sh.slot_fills[sl] > 0) mbar_wait_landed(&sh.full[sl], (uint32_t)((sh.slot_fills[sl] - 1) & 1), L.err);
         }
         __syncwarp();
-    } else if (warp == P_MMA) {
+    } else if (warp == TC_MMA_WARP) {
         // ---------------- MMA issuer ----------------
         if (lane == 0) {
             const uint32_t idesc = idesc_f16(FMT);
@@ -539,7 +491,7 @@ __global__ void __launch_bounds__(32 * (NPROD + 1 + NEPI), (32 * (NPROD + 1 + NE
                     for (int kk = 0; kk < TC_KATOM / 16; kk++)
                         tc_mma(dt, ad + (uint64_t)(2 * kk), bd + (uint64_t)(2 * kk), idesc, (kc > 0 || kk > 0) ? 1u : 0u);
                     issued = true;
-                    if (++slot == NSTAGE) { slot = 0; phase ^= 1; }
+                    if (++slot == TC_STAGES) { slot = 0; phase ^= 1; }
                     if ((kc + 1) % G == 0 || kc + 1 == natoms) {
                         tc_commit(&sh.gbar[q % TC_NGBAR]);          // releases the group's slots; the
                         q++;                                         // unit's last group also readies D
@@ -556,22 +508,18 @@ __global__ void __launch_bounds__(32 * (NPROD + 1 + NEPI), (32 * (NPROD + 1 + NE
         }
         __syncwarp();
     } else {
-        // ---------------- epilogue: the last NEPI warps ----------------
-        // Each thread owns one accumulator row (TMEM lane) and, with 8
-        // epilogue warps, one half of the 256 columns (128-row block
-        // J = 2 Jp + ch of the unit), with 4 both halves in turn.  The h
+        // ---------------- epilogue: warps 5..12 ----------------
+        // Each thread owns one accumulator row (TMEM lane) and one half of
+        // the 256 columns: 128-row block J = 2 Jp + ch of the unit.  The h
         // terms of the next unit are fetched while the current one is
         // tested; the test runs as max_j (g_ij - h_j) > h_i over 32 columns
         // and only a passing chunk is examined element by element.
         const int q4 = warp & 3;                    // tensor-memory lane quarter of this warp
-        const int ch0 = (NEPI == 8) ? ((warp - P_EPI0) >> 2) : 0;   // first column half
+        const int ch = (warp - TC_EPI_WARP0) >> 2;  // column half
         const int row = q4 * 32 + lane;             // accumulator row = TMEM lane
-        const int et = threadIdx.x - 32 * P_EPI0;   // column index for h (NEPI x 32 threads)
-        constexpr int HCPER = TC_N / (32 * NEPI);   // h columns fetched per thread
+        const int et = threadIdx.x - 32 * TC_EPI_WARP0;   // 0..255, column index for h
         const float inf = __int_as_float(0x7f800000);
-        float hc_next[HCPER], hr_next = inf;
-#pragma unroll
-        for (int v = 0; v < HCPER; v++) hc_next[v] = inf;
+        float hc_next = inf, hr_next = inf;
         TcUnit nxt{};
         bool ok0 = mbar_wait(&sh.dfull[0], 0, abort, L.err, wc);
         if (ok0) {
@@ -579,19 +527,17 @@ __global__ void __launch_bounds__(32 * (NPROD + 1 + NEPI), (32 * (NPROD + 1 + NE
             __syncwarp();
             if (lane == 0) mbar_arrive(&sh.dempty[0]);
             if (job.gram_rows == 0) {
-#pragma unroll
-                for (int v = 0; v < HCPER; v++) hc_next[v] = L.H[nxt.rowB + et + v * 32 * NEPI];
+                hc_next = L.H[nxt.rowB + et];
                 hr_next = L.H[nxt.rowA + row];
             }
         }
         for (long long k = 0; k < my_units; k++) {
-            if (epi_bar_or<32 * NEPI>(*abort != 0)) break;   // uniform over the epilogue threads
+            if (epi_bar_or(*abort != 0)) break;              // uniform over the epilogue threads
             const int buf = (int)(k & 1);
             const TcUnit cur = nxt;
-#pragma unroll
-            for (int v = 0; v < HCPER; v++) sh.hc[buf][et + v * 32 * NEPI] = hc_next[v];
+            sh.hc[buf][et] = hc_next;
             const float hr = hr_next;
-            asm volatile("bar.sync 1, %0;" ::"n"(NEPI * 32) : "memory");
+            asm volatile("bar.sync 1, %0;" ::"n"(TC_EPI_WARPS * 32) : "memory");
             if (k + 1 < my_units) {
                 const int ds = (int)((k + 1) % TC_NDESC);
                 if (mbar_wait(&sh.dfull[ds], (uint32_t)(((k + 1) / TC_NDESC) & 1), abort, L.err, wc)) {
@@ -599,8 +545,7 @@ __global__ void __launch_bounds__(32 * (NPROD + 1 + NEPI), (32 * (NPROD + 1 + NE
                     __syncwarp();
                     if (lane == 0) mbar_arrive(&sh.dempty[ds]);
                     if (job.gram_rows == 0) {
-#pragma unroll
-                        for (int v = 0; v < HCPER; v++) hc_next[v] = L.H[nxt.rowB + et + v * 32 * NEPI];
+                        hc_next = L.H[nxt.rowB + et];
                         hr_next = L.H[nxt.rowA + row];
                     }
                 }
@@ -610,58 +555,43 @@ __global__ void __launch_bounds__(32 * (NPROD + 1 + NEPI), (32 * (NPROD + 1 + NE
             ok = __all_sync(0xffffffffu, ok);
             if (!ok) continue;                               // the next loop top stops every warp
             tc_fence_after();
-            // column halves this thread reads: past the Gram rows, or a
-            // lower-triangle block, is skipped; the accumulator is released
-            // after the last half read
-            bool skip[NCH];
-            int last = -1;
-#pragma unroll
-            for (int ci = 0; ci < NCH; ci++) {
-                const int J = 2 * cur.Jp + ch0 + ci;
-                skip[ci] = (job.gram_rows > 0) ? (J * TC_TILE >= job.gram_rows) : (J < cur.I);
-                if (!skip[ci]) last = ci;
-            }
-            if (last < 0) {
+            const int J = 2 * cur.Jp + ch;                   // 128-row block of this thread's columns
+            const bool skip = (job.gram_rows > 0) ? (J * TC_TILE >= job.gram_rows) : (J < cur.I);
+            if (skip) {                                      // past the Gram rows, or a lower-triangle block
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&sh.tempty[buf]);
                 continue;
             }
+            const uint32_t taddr = tbase + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(buf * TC_N + ch * TC_TILE);
+            const bool diag = (J == cur.I);
+            const float *hcs = sh.hc[buf] + ch * TC_TILE;
             SecState *st = (job.gram_rows == 0) ? &L.st[cur.sec] : nullptr;
-#pragma unroll
-            for (int ci = 0; ci < NCH; ci++) {
-                if (skip[ci]) continue;
-                const int ch = ch0 + ci;
-                const int J = 2 * cur.Jp + ch;                   // 128-row block of these columns
-                const uint32_t taddr = tbase + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(buf * TC_N + ch * TC_TILE);
-                const bool diag = (J == cur.I);
-                const float *hcs = sh.hc[buf] + ch * TC_TILE;
-                // two halves of 64 columns: two loads, one wait each; the
-                // accumulator is released once the last half is in registers
-                for (int h = 0; h < 2; h++) {
-                    uint32_t r[64];
-                    tmem_ld32_nowait(taddr + (uint32_t)(h * 64), r);
-                    tmem_ld32_nowait(taddr + (uint32_t)(h * 64 + 32), r + 32);
-                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-                    if (h == 1 && ci == last) {
-                        tc_fence_before();
-                        __syncwarp();
-                        if (lane == 0) mbar_arrive(&sh.tempty[buf]);
-                    }
-                    if (job.gram_rows > 0) {
-                        float *o = job.gram_out + ((int64_t)cur.I * TC_TILE + row) * job.gram_rows + (int64_t)J * TC_TILE + h * 64;
-#pragma unroll
-                        for (int c = 0; c < 64; c++) o[c] = __uint_as_float(r[c]);
-                        continue;
-                    }
-                    screen_test_64(L, st, cur.sec, cur.I, J, row, diag, h, r, hcs, hr);
+            // two halves of 64 columns: two loads, one wait each; the
+            // accumulator is released once the second half is in registers
+            for (int h = 0; h < 2; h++) {
+                uint32_t r[64];
+                tmem_ld32_nowait(taddr + (uint32_t)(h * 64), r);
+                tmem_ld32_nowait(taddr + (uint32_t)(h * 64 + 32), r + 32);
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                if (h == 1) {
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&sh.tempty[buf]);
                 }
+                if (job.gram_rows > 0) {
+                    float *o = job.gram_out + ((int64_t)cur.I * TC_TILE + row) * job.gram_rows + (int64_t)J * TC_TILE + h * 64;
+#pragma unroll
+                    for (int c = 0; c < 64; c++) o[c] = __uint_as_float(r[c]);
+                    continue;
+                }
+                screen_test_64(L, st, cur.sec, cur.I, J, row, diag, h, r, hcs, hr);
             }
         }
     }
 
     tc_fence_before();
     __syncthreads();
-    if (warp == P_MMA) {
+    if (warp == TC_MMA_WARP) {
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(TC_TMEM_COLS) : "memory");
     }
@@ -708,52 +638,34 @@ inline int make_operand_map(CUtensorMap *map, const void *X, int64_t rows, int B
 
 inline bool screen_uses_tcgen05(int precision) { return precision == 1 || precision == 2; }
 
-// The screen's shared-memory size attributes (set once, before any launch;
-// also called before a stream capture).
+// Launch the screen for a level.  `map` must describe L.X.  One persistent
+// CTA per SM (the shared memory admits no second one); `n_cta` caps the
+// grid (the units are dealt out round-robin).
+// The screen's shared-memory size attribute (set once per format, before
+// any launch; also called before a stream capture).
 inline cudaError_t screen_tc_prepare(int precision)
 {
     static bool attr_done[2] = {false, false};
     int fi = precision == 2 ? 1 : 0;
     if (!attr_done[fi]) {
-        cudaError_t e;
-        if (precision == 2) {
-            e = cudaFuncSetAttribute(k_screen_tc<1, TC_PROD_WARPS, TC_STAGES, TC_EPI_WARPS>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM_BYTES);
-            if (e == cudaSuccess)
-                e = cudaFuncSetAttribute(k_screen_tc<1, TC_N_PROD, TC_N_STAGE, TC_N_EPI>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, TC_N_SMEM_BYTES);
-        } else {
-            e = cudaFuncSetAttribute(k_screen_tc<0, TC_PROD_WARPS, TC_STAGES, TC_EPI_WARPS>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM_BYTES);
-            if (e == cudaSuccess)
-                e = cudaFuncSetAttribute(k_screen_tc<0, TC_N_PROD, TC_N_STAGE, TC_N_EPI>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, TC_N_SMEM_BYTES);
-        }
+        cudaError_t e = (precision == 2)
+                            ? cudaFuncSetAttribute(k_screen_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   TC_SMEM_BYTES)
+                            : cudaFuncSetAttribute(k_screen_tc<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   TC_SMEM_BYTES);
         if (e != cudaSuccess) return e;
         attr_done[fi] = true;
     }
     return cudaSuccess;
 }
 
-// Launch the screen for a level.  `map` must describe L.X.  One persistent
-// CTA per SM (the shared memory admits no second one); `n_cta` caps the
-// grid (the units are dealt out round-robin).  L.tc_cfg picks the shape.
 inline cudaError_t launch_screen_tc_map(const LevelDev &L, const CUtensorMap &map, int precision, int n_cta,
                                         cudaStream_t s, TcJob job)
 {
     cudaError_t e = screen_tc_prepare(precision);
     if (e != cudaSuccess) return e;
-    if (L.tc_cfg == 1) {
-        if (precision == 2)
-            k_screen_tc<1, TC_N_PROD, TC_N_STAGE, TC_N_EPI><<<n_cta, TC_N_THREADS, TC_N_SMEM_BYTES, s>>>(L, map, job);
-        else
-            k_screen_tc<0, TC_N_PROD, TC_N_STAGE, TC_N_EPI><<<n_cta, TC_N_THREADS, TC_N_SMEM_BYTES, s>>>(L, map, job);
-    } else {
-        if (precision == 2)
-            k_screen_tc<1, TC_PROD_WARPS, TC_STAGES, TC_EPI_WARPS><<<n_cta, TC_THREADS, TC_SMEM_BYTES, s>>>(L, map, job);
-        else
-            k_screen_tc<0, TC_PROD_WARPS, TC_STAGES, TC_EPI_WARPS><<<n_cta, TC_THREADS, TC_SMEM_BYTES, s>>>(L, map, job);
-    }
+    if (precision == 2) k_screen_tc<1><<<n_cta, TC_THREADS, TC_SMEM_BYTES, s>>>(L, map, job);
+    else k_screen_tc<0><<<n_cta, TC_THREADS, TC_SMEM_BYTES, s>>>(L, map, job);
     return cudaGetLastError();
 }
 

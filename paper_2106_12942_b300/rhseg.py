@@ -20,8 +20,7 @@ CUDA-event times in stats()); wait_cycles (bound of the tensor-core screen's
 pipeline waits in clock cycles, 0 = the default of about 2 s; a wait that
 runs out makes run() raise RHSEGError with code RHSEG_ETIMEOUT); screen_group
 (K slices per tcgen05.commit of the tensor-core screen, 0 = default; chosen by
-the autotuner, results identical); overlap (1: the even and odd sections of a
-level on two overlapping streams instead of one; results identical).
+the autotuner, results identical).
 """
 from __future__ import annotations
 
@@ -33,7 +32,7 @@ from . import _abi
 
 DEFAULTS = dict(rnb_levels=1, conv_nregions=1, spclust_wght=0.0, connectivity=8, min_nregions=0,
                 n_out_levels=1, seam_pass=1, precision=1, profile=0, incremental=0,
-                multi_merge=0, wait_cycles=0, screen_group=0, overlap=0)
+                multi_merge=0, wait_cycles=0, screen_group=0)
 
 
 class RHSEGError(RuntimeError):
