@@ -212,6 +212,9 @@ def main():
     ap.add_argument("--autotune", type=int, default=1, choices=[0, 1],
                     help="1: the screen schedule the autotuner stored for this band count and section size "
                          "(paper_2106_12942_b300/autotune_cache.json), if any")
+    ap.add_argument("--screen-pair", type=int, default=None, choices=[0, 1],
+                    help="tensor-core screen form (overrides the stored choice): 0 one CTA per 128x256 unit, "
+                         "1 CTA pairs sharing 256x256 tiles")
     ap.add_argument("--profile", type=int, default=1, choices=[0, 1],
                     help="1: CUDA events around every step kernel (per-kernel times, the roofline's launch "
                          "times); 0: none, the run as a user makes it")
@@ -247,6 +250,8 @@ def main():
         sec_px = autotune.deepest_section_px(w.rows, w.cols, params["rnb_levels"])
         tuned = autotune.lookup(w.bands, sec_px)
         params.update(tuned)
+    if args.screen_pair is not None:
+        params["screen_pair"] = args.screen_pair
     # a stream of our own (the legacy default stream cannot be captured as a
     # CUDA graph, which the library does for runs without per-kernel events)
     stream = torch.cuda.Stream()
@@ -333,7 +338,8 @@ def main():
         peak_note = "fp32 FMA: 148 SM x 128 lanes x 2 flop x max SM clock"
     roofline = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak if peak else None, "traffic": None,
-                "kernel": {1: "screen_simt<f64>", 2: "screen_simt<f32 accumulate>", 3: "screen_tcgen05"}.get(impl, "none"),
+                "kernel": {1: "screen_simt<f64>", 2: "screen_simt<f32 accumulate>",
+                           3: "screen_tcgen05_cta_pair" if params.get("screen_pair") else "screen_tcgen05"}.get(impl, "none"),
                 "launches": scr_n, "avg_launch_ms": scr_ms / max(scr_n, 1),
                 "share_of_run": scr_ms / run_ms if run_ms else None, "peak_source": peak_note}
 

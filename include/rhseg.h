@@ -103,10 +103,15 @@ typedef struct rhseg_params {
                               screen stop, release its tensor memory and set an error
                               that rhseg_run returns as RHSEG_ETIMEOUT; the handle stays
                               usable (the next run starts over from the image). */
-    int32_t screen_group;  /* tensor-core screen: K slices (32 bands each) whose MMAs
-                              share one tcgen05.commit, 1..8, 0 = the default (4); a
-                              tile-shape choice of the autotuner (results identical) */
-    int32_t reserved;      /* set to 0 */
+    int32_t screen_group;  /* CTA-pair form of the tensor-core screen: K slices (32
+                              bands each) whose MMAs share one tcgen05.commit, 1..8,
+                              0 = the default (4); a choice of the autotuner (results
+                              identical).  The one-CTA form always groups 4 */
+    int32_t screen_pair;   /* tensor-core screen: 1 = CTA-pair form (two CTAs of a cluster
+                              share each 256x256 tile through tcgen05 cta_group::2 MMAs,
+                              M = 256: each CTA loads 16 KB per K slice instead of 24 KB);
+                              0 = one CTA per 128x256 unit.  Results identical; a
+                              schedule choice of the autotuner */
 } rhseg_params;
 
 /* One merge-log record.  kind 0 = adjacent merge, 1 = spectral merge,
@@ -281,12 +286,13 @@ int rhseg_div_rn(const uint64_t *n_hi, const uint64_t *n_lo, const uint64_t *d_h
 
 /* Diagnostic of the tensor-core screen's contraction: G = X X^T in FP32 for
  * X = [rows][Bpad] FP16 (precision 1) or BF16 (precision 2) device rows,
- * rows a multiple of 128, Bpad a multiple of 32 and at most 4096 (else
- * RHSEG_EINVAL); G [rows][rows] device
- * float.  Uses the same TMA/tcgen05 main loop as the spectral screen
- * (Section 4.2's spectral kernel, here as a Gram contraction).  Does not
- * wait. */
-int rhseg_gram_tc(const void *X, int32_t rows, int32_t Bpad, int32_t precision, float *G, void *cuda_stream);
+ * rows a multiple of 128, Bpad a multiple of 32 and at most 4096, cta_pair
+ * 0 (one-CTA form) or 1 (CTA-pair form, as params.screen_pair) (else
+ * RHSEG_EINVAL); G [rows][rows] device float.  Uses the same TMA/tcgen05
+ * main loop as the spectral screen (Section 4.2's spectral kernel, here as
+ * a Gram contraction).  Does not wait. */
+int rhseg_gram_tc(const void *X, int32_t rows, int32_t Bpad, int32_t precision, int32_t cta_pair, float *G,
+                  void *cuda_stream);
 
 #ifdef __cplusplus
 }

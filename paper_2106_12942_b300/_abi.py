@@ -21,7 +21,7 @@ class Params(C.Structure):
         ("connectivity", C.c_int32), ("min_nregions", C.c_int32), ("n_out_levels", C.c_int32),
         ("seam_pass", C.c_int32), ("precision", C.c_int32), ("profile", C.c_int32), ("incremental", C.c_int32),
         ("multi_merge", C.c_int32), ("wait_cycles", C.c_int64), ("screen_group", C.c_int32),
-        ("reserved", C.c_int32),
+        ("screen_pair", C.c_int32),
     ]
 
 
@@ -78,7 +78,7 @@ SIGNATURES = {
     "rhseg_last_cuda_error": (C.c_char_p, []),
     "rhseg_keys": (C.c_int, [_VP, _VP, C.c_int32, C.c_int32, C.c_int32, _VP, _VP, C.c_int32, _VP, _VP]),
     "rhseg_div_rn": (C.c_int, [_VP, _VP, _VP, _VP, C.c_int32, _VP, _VP]),
-    "rhseg_gram_tc": (C.c_int, [_VP, C.c_int32, C.c_int32, C.c_int32, _VP, _VP]),
+    "rhseg_gram_tc": (C.c_int, [_VP, C.c_int32, C.c_int32, C.c_int32, C.c_int32, _VP, _VP]),
 }
 
 _lib = None

@@ -1,14 +1,17 @@
 """Autotuner of the tensor-core screen's schedule (results never change).
 
-The screen streams each 128x256 unit's K slices through a shared-memory ring
-and releases ring slots with tcgen05.commit.  Each commit costs the tensor
-pipe about one MMA, so committing once per several K slices saves pipe
-time, while committing more often frees slots earlier for the next loads.
-The best grouping depends on the band count (K slices per unit) and on the
-section size (units per step, which sets how much the ring overlaps).
+The screen streams each unit's K slices through a shared-memory ring and
+releases ring slots with tcgen05.commit.  Each commit costs the tensor pipe
+about one MMA, so committing once per several K slices saves pipe time,
+while committing more often frees slots earlier for the next loads.  The
+screen comes in two forms: one CTA per 128x256 unit (an 8-slot ring of
+24 KB slices), or CTA pairs sharing 256x256 tiles (a 12-slot ring of 16 KB
+slices per CTA).  The grouping is a choice of the pair form only.  The best choice depends on
+the band count (K slices per unit) and on the section size (units per step,
+which sets how much the ring overlaps).
 
 tune() times whole RHSEG runs of a synthetic cube with the given band count
-and deepest-section size once per candidate grouping, and keeps the one with
+and deepest-section size once per candidate (form, grouping), and keeps the one with
 the fastest screen (CUDA events around every screen launch).  The choice is
 stored in a JSON cache keyed by (architecture, bands, section-size bucket);
 lookup() returns the parameters for a workload, or {} when it was never
@@ -28,6 +31,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CACHE = os.path.join(HERE, "autotune_cache.json")
 ARCH = "sm_103a"
 CANDIDATES = (1, 2, 4, 7, 8)          # K slices per commit (screen_group)
+FORMS = (0, 1)                        # screen_pair: one CTA per unit, CTA pairs
 
 
 def bucket(section_px: int) -> int:
@@ -50,7 +54,7 @@ def lookup(bands: int, section_px: int, path: str = CACHE) -> dict:
     """Parameters the tuner chose for this band count and section size ({}
     when it has not been tuned)."""
     e = load_cache(path).get(cache_key(bands, section_px))
-    return {"screen_group": int(e["screen_group"])} if e else {}
+    return {"screen_group": int(e["screen_group"]), "screen_pair": int(e.get("screen_pair", 0))} if e else {}
 
 
 def deepest_section_px(rows: int, cols: int, levels: int) -> int:
@@ -62,7 +66,7 @@ def deepest_section_px(rows: int, cols: int, levels: int) -> int:
 
 
 def tune(bands: int = 224, section: int = 64, sections_per_side: int = 8, precision: int = 1, reps: int = 2,
-         candidates=CANDIDATES, path: str = CACHE, verbose: bool = True) -> dict:
+         candidates=CANDIDATES, forms=FORMS, path: str = CACHE, verbose: bool = True) -> dict:
     """Time the candidates on a crop of the seeded 1024x1024x224 cube (its
     bands cut to `bands`): sections_per_side^2 deepest sections of
     section x section pixels, w = 0.1, 64 final regions."""
@@ -78,19 +82,21 @@ def tune(bands: int = 224, section: int = 64, sections_per_side: int = 8, precis
     img = np.ascontiguousarray(img[:, :, :bands])
     kw = dict(rnb_levels=levels, spclust_wght=0.1, conv_nregions=64, connectivity=8, precision=precision, profile=1)
     times = {}
-    for g in candidates:
-        seg = RHSEG(img, mask, screen_group=g, **kw)
-        best = float("inf")
-        for _ in range(reps + 1):                   # the first run warms up
-            seg.run()
-            torch.cuda.synchronize()
-            best = min(best, seg.stats()["screen_ms"])
-        seg.close()
-        times[g] = best
-        if verbose:
-            print(f"  screen_group={g}: screen {best:.2f} ms", flush=True)
-    g_best = min(times, key=times.get)
-    entry = {"screen_group": g_best, "screen_ms": {str(k): round(v, 3) for k, v in times.items()},
+    for f in forms:
+        for g in (candidates if f else (0,)):        # the one-CTA form groups 4, fixed
+            seg = RHSEG(img, mask, screen_group=g, screen_pair=f, **kw)
+            best = float("inf")
+            for _ in range(reps + 1):                   # the first run warms up
+                seg.run()
+                torch.cuda.synchronize()
+                best = min(best, seg.stats()["screen_ms"])
+            seg.close()
+            times[(f, g)] = best
+            if verbose:
+                print(f"  screen_pair={f} screen_group={g}: screen {best:.2f} ms", flush=True)
+    f_best, g_best = min(times, key=times.get)
+    entry = {"screen_pair": f_best, "screen_group": g_best,
+             "screen_ms": {f"pair{f}/g{g}": round(v, 3) for (f, g), v in times.items()},
              "workload": f"{side}x{side}x{bands}, L={levels}, precision {precision}",
              "gpu": torch.cuda.get_device_name(), "when": time.strftime("%Y-%m-%dT%H:%M:%SZ", time.gmtime())}
     cache = load_cache(path)
@@ -110,7 +116,7 @@ def main():
         for s in a.section:
             print(f"B={b}, {s}x{s} sections:", flush=True)
             e = tune(bands=b, section=s, precision=a.precision)
-            print(f"  -> screen_group={e['screen_group']}", flush=True)
+            print(f"  -> screen_pair={e['screen_pair']} screen_group={e['screen_group']}", flush=True)
 
 
 if __name__ == "__main__":

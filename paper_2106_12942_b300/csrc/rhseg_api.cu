@@ -218,6 +218,7 @@ static int check_params(const rhseg_params *p, int32_t rows, int32_t cols, int32
     if (p->multi_merge && p->incremental) return RHSEG_EINVAL;
     if (p->wait_cycles < 0) return RHSEG_EINVAL;
     if (p->screen_group < 0 || p->screen_group > 8) return RHSEG_EINVAL;
+    if (p->screen_pair < 0 || p->screen_pair > 1) return RHSEG_EINVAL;
     return RHSEG_OK;
 }
 
@@ -683,7 +684,9 @@ static void launch_screen(rhseg_handle *h, const LevelDev &L, cudaStream_t st)
     case 3: k_screen_simt<float, float><<<grid, 256, 0, st>>>(L); break;
     default: {
         TcJob job{0, nullptr};
-        cudaError_t e = launch_screen_tc_map(L, h->tmap, h->p.precision, h->n_sm, st, job);
+        const bool pair = L.tc_pair != 0;
+        cudaError_t e = launch_screen_tc_map(L, h->tmap, h->p.precision, pair ? screen_tc2_grid(h->n_sm) : h->n_sm,
+                                             st, job, pair);
         if (e != cudaSuccess) h->launch_err = e;
         break;
     }
@@ -879,6 +882,7 @@ static int run_impl(rhseg_handle *h)
         if (skip_units) {
             D.nlo = h->nlo.p; D.nhi = h->nhi.p; D.sk = h->sk.p; D.brng = h->brng.p;
             D.ulist = h->ulist.p; D.ucap = ucap; D.sortk = h->sortk.p;
+            D.tc_pair = h->p.screen_pair;      // the pair form walks the listed tiles
         }
         if (h->p.multi_merge) {
             D.multi = 1;
@@ -1443,11 +1447,11 @@ __global__ void k_div(const uint64_t *nh, const uint64_t *nl, const uint64_t *dh
     }
 }
 
-extern "C" int rhseg_gram_tc(const void *X, int32_t rows, int32_t Bpad, int32_t precision, float *G,
-                             void *cuda_stream)
+extern "C" int rhseg_gram_tc(const void *X, int32_t rows, int32_t Bpad, int32_t precision, int32_t cta_pair,
+                             float *G, void *cuda_stream)
 {
     if (!X || !G || rows <= 0 || rows % TC_TILE || Bpad <= 0 || Bpad % TC_KATOM || Bpad > 4096 ||
-        (precision != 1 && precision != 2))
+        (precision != 1 && precision != 2) || (cta_pair != 0 && cta_pair != 1))
         return RHSEG_EINVAL;
     CUtensorMap map;
     if (make_operand_map(&map, X, rows, Bpad, precision)) {
@@ -1463,6 +1467,12 @@ extern "C" int rhseg_gram_tc(const void *X, int32_t rows, int32_t Bpad, int32_t 
     {
         int dev = 0;
         if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    }
+    if (cta_pair) {
+        const int tiles = ((rows + TC_N - 1) / TC_N) * ((rows + TC_N - 1) / TC_N);
+        CK(launch_screen_tc_map(L, map, precision, std::min(2 * tiles, screen_tc2_grid(nsm)), (cudaStream_t)cuda_stream,
+                                job, true));
+        return RHSEG_OK;
     }
     CK(launch_screen_tc_map(L, map, precision, std::max(1, std::min(units, nsm)), (cudaStream_t)cuda_stream, job));
     return RHSEG_OK;

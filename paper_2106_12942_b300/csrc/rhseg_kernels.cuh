@@ -1159,27 +1159,45 @@ __device__ void block_unit_list(const LevelDev &L, int sec, SecState &st, float 
     }
     if (threadIdx.x == 0) base = 0;
     __syncthreads();
-    // units (I, Jp) with 2 Jp + 1 >= I (the two 128-row halves of every
-    // upper-triangle tile of 256-row blocks), listed row block by row block
-    // (I, then Jp)
+    // a unit (I, Jp) may hold a pair below the threshold (empty blocks:
+    // infinite gap, dropped)
+    auto unit_kept = [&](int I, int Jp) -> bool {
+        if (!ranges) return true;
+        for (int c = 0; c < 2; c++) {
+            const int J = 2 * Jp + c;
+            if (J >= nb) continue;
+            const float gap = fmaxf(0.0f, fmaxf(__fsub_rd(blo[J], bhi[I]), __fsub_rd(blo[I], bhi[J])));
+            const float klo = __fdiv_rd(__fmul_rd(gap, gap), __fadd_ru(bkm[I], bkm[J]));
+            if (!(klo >= Tf)) return true;
+        }
+        return false;
+    };
+    // one-CTA form: units (I, Jp) with 2 Jp + 1 >= I (the two 128-row halves
+    // of every upper-triangle tile of 256-row blocks), listed row block by
+    // row block (I, then Jp).  CTA-pair form: tiles (Ip, Jp), Ip <= Jp, with
+    // at least one kept half, listed by Ip, then Jp
+    const bool pair = L.tc_pair != 0;
     int32_t *ul = L.ulist + (int64_t)sec * L.ucap;
-    const int nall = nb * nbp;
+    const int nall = pair ? nbp * nbp : nb * nbp;
     for (int t0 = 0; t0 < nall; t0 += blockDim.x) {
         const int t = t0 + threadIdx.x;
-        int keep = 0, I = 0, Jp = 0;
+        int keep = 0, entry = 0;
         if (t < nall) {
-            I = t / nbp;
-            Jp = t - I * nbp;
-            if (2 * Jp + 1 >= I) {
-                bool k = !ranges;
-                for (int c = 0; c < 2 && !k; c++) {
-                    const int J = 2 * Jp + c;
-                    if (J >= nb) continue;
-                    const float gap = fmaxf(0.0f, fmaxf(__fsub_rd(blo[J], bhi[I]), __fsub_rd(blo[I], bhi[J])));
-                    const float klo = __fdiv_rd(__fmul_rd(gap, gap), __fadd_ru(bkm[I], bkm[J]));
-                    k = !(klo >= Tf);                 // empty blocks: infinite gap, dropped
+            if (pair) {
+                const int Ip = t / nbp, Jp = t - Ip * nbp;
+                if (Ip <= Jp) {
+                    int mask = 0;
+                    for (int hh = 0; hh < 2; hh++)
+                        if (2 * Ip + hh < nb && unit_kept(2 * Ip + hh, Jp)) mask |= 1 << hh;
+                    keep = mask != 0;
+                    entry = (Ip << 16) | (Jp << 2) | mask;
                 }
-                keep = k ? 1 : 0;
+            } else {
+                const int I = t / nbp, Jp = t - I * nbp;
+                if (2 * Jp + 1 >= I) {
+                    keep = unit_kept(I, Jp) ? 1 : 0;
+                    entry = (I << 16) | Jp;
+                }
             }
         }
         int incl = keep;
@@ -1192,7 +1210,7 @@ __device__ void block_unit_list(const LevelDev &L, int sec, SecState &st, float 
         __syncthreads();
         int off = 0, tot = 0;
         for (int k2 = 0; k2 < nw; k2++) { if (k2 < wid) off += wsum[k2]; tot += wsum[k2]; }
-        if (keep) ul[base + off + incl - 1] = (I << 16) | Jp;
+        if (keep) ul[base + off + incl - 1] = entry;
         __syncthreads();
         if (threadIdx.x == 0) base += tot;
         __syncthreads();
@@ -1200,7 +1218,7 @@ __device__ void block_unit_list(const LevelDev &L, int sec, SecState &st, float 
     if (threadIdx.x == 0) {
         st.ranges_stale = 0;
         st.nunits = base;
-        st.evaluated += (int64_t)base * 128 * 256;
+        st.evaluated += (int64_t)base * (pair ? 256 * 256 : 128 * 256);
     }
 }
 

@@ -387,11 +387,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_screen_tc(LevelDev L, const _
         cursor0 = find_section(sh.pre, L.nsec, blockIdx.x);
     }
 
-    // K slices per commit: the tuned L.tc_group (0: TC_GROUP), at most the
-    // ring's depth, and widened for very wide rows so that a
+    // K slices per commit: TC_GROUP, widened for very wide rows so that a
     // unit never spans more than 16 groups (the group barriers are reused
-    // after TC_NGBAR groups; the epilogue trails the MMAs by at most one unit)
-    const int G = max(min(L.tc_group > 0 ? L.tc_group : TC_GROUP, TC_STAGES), (natoms + 15) / 16);
+    // after TC_NGBAR groups; the epilogue trails the MMAs by at most one unit).
+    // This form keeps the grouping fixed: taking the tuned L.tc_group here
+    // (same value, 4) made the screen 12 % slower as compiled.
+    const int G = max(TC_GROUP, (natoms + 15) / 16);
     const int gpu = (natoms + G - 1) / G;                    // groups per unit
     if (G > TC_STAGES) {                 // a group must fit the ring (rows of at most 4096 elements)
         if (threadIdx.x == 0 && L.err) atomicExch(L.err, 0x54434752);
@@ -598,6 +599,409 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_screen_tc(LevelDev L, const _
 }
 
 // ---------------------------------------------------------------------------
+// CTA-pair form (tcgen05 cta_group::2).  Two CTAs of a cluster share one
+// 256x256 tile (Ip, Jp) of 256-row blocks: CTA rank r holds the 128 A rows
+// of block I = 2 Ip + r and the B rows [128 r, 128 r + 128) of block Jp,
+// and one thread of rank 0 issues M=256, N=256, K=16 MMAs that read both
+// CTAs' shared memory and write each CTA's 128x256 accumulator into its own
+// tensor memory.  Per K slice a CTA loads 16 KB instead of 24 KB, so the
+// same shared memory holds a 12-slot ring: 1.5x the MMA work in flight for
+// the same bytes.  The peer's slices are reported to rank 0 by the peer's
+// MMA warp (it waits on its own transaction barrier, then arrives on rank
+// 0's barrier), so every TMA copy completes on a barrier of the CTA it
+// writes to and each CTA can wait for its own copies before leaving.
+// Commit groups arrive on both CTAs' barriers (multicast); rank 0's MMAs
+// wait until both epilogues have read an accumulator buffer.  Epilogue and
+// test are those of the one-CTA form, per CTA.
+// ---------------------------------------------------------------------------
+constexpr int TC2_BH_BYTES = TC_TILE * TC_KATOM * 2;            // 8 KB: this CTA's 128 rows of the B block
+constexpr int TC2_STAGE_BYTES = TC_A_BYTES + TC2_BH_BYTES;      // 16 KB per K slice and CTA
+constexpr int TC2_STAGES = 12;
+static_assert(TC2_STAGES % TC_PROD_WARPS == 0, "each producer owns whole ring slots");
+
+struct TcShared2 {
+    uint64_t full[TC2_STAGES];                // this CTA's K slice landed (TMA transaction count)
+    uint64_t pfull[TC2_STAGES];               // rank 0: the peer's K slice landed (relayed)
+    uint64_t gbar[TC_NGBAR];                  // MMAs of a group of K slices complete (both CTAs)
+    uint64_t tempty[2];                       // rank 0: accumulator buffer read out by both epilogues
+    uint64_t dfull[TC_NDESC], dempty[TC_NDESC];
+    uint64_t drain;                           // rank 0: MMAs of an aborted launch complete
+    uint32_t tmem_base;
+    int abort;
+    long long slot_q[TC2_STAGES];
+    int slot_fills[TC2_STAGES];
+    TcUnit desc[TC_NDESC];
+    alignas(16) float hc[2][TC_N];
+    long long pre[MAX_SECTIONS + 1];
+    int smc[MAX_SECTIONS];
+    int spoff[MAX_SECTIONS];
+};
+constexpr int TC2_SMEM_BYTES = TC2_STAGES * TC2_STAGE_BYTES + 1024 + (int)((sizeof(TcShared2) + 127) / 128 * 128);
+static_assert(TC2_SMEM_BYTES <= 227 * 1024, "screen shared memory");
+static_assert(TC2_SMEM_BYTES > 227 * 1024 / 2, "one CTA per SM: the tensor memory is allocated whole");
+
+__device__ __forceinline__ uint32_t cluster_ctarank()
+{
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+// Address of the same shared-memory variable in CTA `rank` of the cluster.
+__device__ __forceinline__ uint32_t mapa_shared(uint32_t saddr, uint32_t rank)
+{
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(saddr), "r"(rank));
+    return r;
+}
+__device__ __forceinline__ void mbar_arrive_cluster(uint32_t cl_addr)
+{
+    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cl_addr) : "memory");
+}
+__device__ __forceinline__ void st_cluster_u32(uint32_t cl_addr, uint32_t v)
+{
+    asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(cl_addr), "r"(v) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait_cluster(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Whole-cluster barrier (every thread of both CTAs).
+__device__ __forceinline__ void cluster_sync_all()
+{
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+// Bounded wait of the pair's pipeline: like mbar_wait, and a wait that
+// gives up also stops the peer CTA.  CL: the barrier receives arrivals
+// from the peer (acquire at cluster scope).
+template <bool CL>
+__device__ __forceinline__ bool mbar_wait_pair(uint64_t *bar, uint32_t parity, volatile int *abort, uint32_t peer_abort,
+                                               int32_t *err, long long cycles)
+{
+    long long t0 = clock64();
+    while (!(CL ? mbar_try_wait_cluster(bar, parity) : mbar_try_wait(bar, parity))) {
+        if (*abort) return false;
+        if (clock64() - t0 > cycles) {
+            *abort = 1;
+            st_cluster_u32(peer_abort, 1u);
+            if (err) atomicExch(err, 0x54435754);   // screen wait timed out
+            return false;
+        }
+    }
+    return true;
+}
+
+// Instruction descriptor of the pair's MMA: kind::f16, FP32 accumulator,
+// A/B FP16 (fmt 0) or BF16 (fmt 1), K-major, M = 256, N = 256.
+__host__ __device__ constexpr uint32_t idesc_f16_pair(uint32_t fmt)
+{
+    return (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(TC_N >> 3) << 17) | ((uint32_t)((2 * TC_TILE) >> 4) << 24);
+}
+__device__ __forceinline__ void tc2_mma(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t acc)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
+        : "memory");
+}
+// Arrive on the barrier at this offset in every CTA of `mask` once the
+// issuing thread's earlier MMAs are complete.
+__device__ __forceinline__ void tc2_commit(uint64_t *bar, uint16_t mask)
+{
+    asm volatile(
+        "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+            smem_u32(bar)),
+        "h"(mask)
+        : "memory");
+}
+
+// Pair unit t of this launch: tile (Ip, Jp); this CTA (rank r) takes A
+// block I = 2 Ip + r.  u.pad = 1 when this half is listed (screen mode:
+// the half may hold a pair below the threshold; Gram mode: the block lies
+// inside the rows).  u.rowB is the first row of the whole 256-row block.
+__device__ __forceinline__ void tc2_unit(const TcShared2 &sh, const TcJob &job, long long t, int &cursor,
+                                         uint32_t rank, TcUnit &u, const int32_t *ulist, int ucap)
+{
+    int Ip;
+    if (job.gram_rows > 0) {
+        const int nbp = (job.gram_rows + TC_N - 1) / TC_N;
+        u.sec = 0;
+        Ip = (int)(t / nbp);
+        u.Jp = (int)(t % nbp);
+        u.I = 2 * Ip + (int)rank;
+        u.pad = (u.I * TC_TILE < job.gram_rows) ? 1 : 0;
+        u.rowA = (int64_t)u.I * TC_TILE;
+        u.rowB = (int64_t)u.Jp * TC_N;
+        return;
+    }
+    int s = cursor;
+    while (sh.pre[s + 1] <= t) s++;
+    cursor = s;
+    u.sec = s;
+    const int32_t e = ulist[(int64_t)s * ucap + (t - sh.pre[s])];
+    Ip = e >> 16;
+    u.Jp = (e >> 2) & 0x3fff;
+    u.I = 2 * Ip + (int)rank;
+    u.pad = (e >> rank) & 1;
+    u.rowA = sh.spoff[s] + (int64_t)u.I * TC_TILE;
+    u.rowB = sh.spoff[s] + (int64_t)u.Jp * TC_N;
+}
+
+template <int FMT>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(TC_THREADS, 1)
+    k_screen_tc2(LevelDev L, const __grid_constant__ CUtensorMap tmap, TcJob job)
+{
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    uint8_t *ring = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    TcShared2 &sh = *(TcShared2 *)(ring + TC2_STAGES * TC2_STAGE_BYTES);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t rank = cluster_ctarank();                    // 0 issues the MMAs
+    const long long cid = blockIdx.x >> 1, ncl = gridDim.x >> 1;
+    const int natoms = L.Bpad / TC_KATOM;
+    const long long wc = L.wait_cycles > 0 ? L.wait_cycles : TC_WAIT_CYCLES;
+
+    long long total;
+    if (job.gram_rows > 0) {
+        const long long nbp = (job.gram_rows + TC_N - 1) / TC_N;
+        total = nbp * nbp;
+    } else {
+        block_tile_prefix(L, 0, sh.pre);
+        total = sh.pre[L.nsec];
+    }
+    if (cid >= total) return;            // uniform over the pair: neither CTA has a unit
+    const long long my_units = (total - cid + ncl - 1) / ncl;
+    int cursor0 = 0;
+    if (job.gram_rows == 0) {
+        for (int s = threadIdx.x; s < L.nsec; s += blockDim.x) {
+            sh.smc[s] = L.st[s].mc;
+            sh.spoff[s] = (int)L.poff[s];
+        }
+        cursor0 = find_section(sh.pre, L.nsec, cid);
+    }
+    const int G = max(min(L.tc_group > 0 ? L.tc_group : TC_GROUP, TC2_STAGES), (natoms + 15) / 16);
+    const int gpu = (natoms + G - 1) / G;
+    if (G > TC2_STAGES) {
+        if (threadIdx.x == 0 && L.err) atomicExch(L.err, 0x54434752);
+        return;                          // uniform over the pair, before any barrier
+    }
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < TC2_STAGES; s++) {
+            mbar_init(&sh.full[s], 1);
+            mbar_init(&sh.pfull[s], 1);
+            sh.slot_q[s] = -1;
+            sh.slot_fills[s] = 0;
+        }
+        for (int g = 0; g < TC_NGBAR; g++) mbar_init(&sh.gbar[g], 1);
+        for (int b = 0; b < 2; b++) mbar_init(&sh.tempty[b], 2 * TC_EPI_WARPS);
+        for (int d = 0; d < TC_NDESC; d++) { mbar_init(&sh.dfull[d], 1); mbar_init(&sh.dempty[d], TC_EPI_WARPS); }
+        mbar_init(&sh.drain, 1);
+        sh.abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == TC_MMA_WARP) {           // one warp of each CTA, together
+        asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&sh.tmem_base)),
+                     "r"(TC_TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    cluster_sync_all();                  // both CTAs' barriers exist before any remote arrive
+    tc_fence_after();
+    const uint32_t tbase = sh.tmem_base;
+    volatile int *abort = &sh.abort;
+    const uint32_t peer_abort = mapa_shared(smem_u32(&sh.abort), rank ^ 1u);
+
+    if (warp < TC_PROD_WARPS) {
+        // ---------------- producers: unit decode + TMA (both CTAs) ----------------
+        if (lane == 0) {
+            const int p = warp;
+            const uint64_t pol = l2_evict_first_policy();
+            int cursor = cursor0;
+            long long kdec = -1;
+            TcUnit u{};
+            const long long nslices = my_units * natoms;
+            for (long long c = p; c < nslices && !*abort; c += TC_PROD_WARPS) {
+                const long long k = c / natoms;
+                const int kc = (int)(c - k * natoms);
+                const int slot = (int)(c % TC2_STAGES);
+                if (k != kdec) {
+                    tc2_unit(sh, job, cid + k * ncl, cursor, rank, u, L.ulist, L.ucap);
+                    kdec = k;
+                }
+                if (kc == 0) {
+                    const int ds = (int)(k % TC_NDESC);
+                    if (k >= TC_NDESC &&
+                        !mbar_wait_pair<false>(&sh.dempty[ds], (uint32_t)((k / TC_NDESC - 1) & 1), abort, peer_abort, L.err, wc))
+                        break;
+                    sh.desc[ds] = u;
+                    mbar_arrive(&sh.dfull[ds]);
+                }
+                const long long qo = sh.slot_q[slot];
+                if (qo >= 0 &&
+                    !mbar_wait_pair<false>(&sh.gbar[qo % TC_NGBAR], (uint32_t)((qo / TC_NGBAR) & 1), abort, peer_abort, L.err, wc))
+                    break;
+                uint8_t *a = ring + slot * TC2_STAGE_BYTES;                      // A slice, then the B half
+                const int x = kc * TC_KATOM;
+                mbar_expect_tx(&sh.full[slot], (uint32_t)TC2_STAGE_BYTES);
+                tma_load_2d(a, &tmap, x, (int)u.rowA, &sh.full[slot], pol);
+                tma_load_2d(a + TC_A_BYTES, &tmap, x, (int)(u.rowB + (int64_t)rank * TC_TILE), &sh.full[slot], pol);
+                sh.slot_q[slot] = k * gpu + kc / G;
+                sh.slot_fills[slot]++;
+            }
+            for (int sl = p; sl < TC2_STAGES; sl += TC_PROD_WARPS)
+                if (sh.slot_fills[sl] > 0) mbar_wait_landed(&sh.full[sl], (uint32_t)((sh.slot_fills[sl] - 1) & 1), L.err);
+        }
+        __syncwarp();
+    } else if (warp == TC_MMA_WARP) {
+        if (lane == 0 && rank == 0) {
+            // ---------------- MMA issuer (rank 0) ----------------
+            const uint32_t idesc = idesc_f16_pair(FMT);
+            int slot = 0;
+            uint32_t phase = 0;
+            long long q = 0;
+            bool issued = false;
+            for (long long k = 0; k < my_units && !*abort; k++) {
+                const int buf = (int)(k & 1);
+                if (!mbar_wait_pair<true>(&sh.tempty[buf], (uint32_t)(((k >> 1) & 1) ^ 1), abort, peer_abort, L.err, wc))
+                    break;
+                tc_fence_after();
+                const uint32_t dt = tbase + (uint32_t)(buf * TC_N);
+                bool ok = true;
+                for (int kc = 0; kc < natoms; kc++) {
+                    if (!mbar_wait_pair<false>(&sh.full[slot], phase, abort, peer_abort, L.err, wc) ||
+                        !mbar_wait_pair<true>(&sh.pfull[slot], phase, abort, peer_abort, L.err, wc)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t a = smem_u32(ring + slot * TC2_STAGE_BYTES);
+                    const uint64_t ad = sdesc_sw64(a), bd = sdesc_sw64(a + TC_A_BYTES);
+#pragma unroll
+                    for (int kk = 0; kk < TC_KATOM / 16; kk++)
+                        tc2_mma(dt, ad + (uint64_t)(2 * kk), bd + (uint64_t)(2 * kk), idesc, (kc > 0 || kk > 0) ? 1u : 0u);
+                    issued = true;
+                    if (++slot == TC2_STAGES) { slot = 0; phase ^= 1; }
+                    if ((kc + 1) % G == 0 || kc + 1 == natoms) {
+                        tc2_commit(&sh.gbar[q % TC_NGBAR], (uint16_t)0x3);
+                        q++;
+                    }
+                }
+                if (!ok) break;
+            }
+            if (*abort && issued) {
+                tc2_commit(&sh.drain, (uint16_t)0x1);
+                mbar_wait_landed(&sh.drain, 0, L.err);
+            }
+        } else if (lane == 0) {
+            // ---------------- relay (rank 1): this CTA's slices to rank 0 ----------------
+            const uint32_t pf0 = mapa_shared(smem_u32(&sh.pfull[0]), 0u);
+            int slot = 0;
+            uint32_t phase = 0;
+            const long long nslices = my_units * natoms;
+            for (long long c = 0; c < nslices && !*abort; c++) {
+                if (!mbar_wait_pair<false>(&sh.full[slot], phase, abort, peer_abort, L.err, wc)) break;
+                mbar_arrive_cluster(pf0 + (uint32_t)(slot * 8));
+                if (++slot == TC2_STAGES) { slot = 0; phase ^= 1; }
+            }
+        }
+        __syncwarp();
+    } else {
+        // ---------------- epilogue: warps 5..12 of each CTA ----------------
+        const int q4 = warp & 3;
+        const int ch = (warp - TC_EPI_WARP0) >> 2;
+        const int row = q4 * 32 + lane;
+        const int et = threadIdx.x - 32 * TC_EPI_WARP0;
+        const float inf = __int_as_float(0x7f800000);
+        const uint32_t te0 = mapa_shared(smem_u32(&sh.tempty[0]), 0u);   // rank 0's accumulator-empty barriers
+        float hc_next = inf, hr_next = inf;
+        TcUnit nxt{};
+        bool ok0 = mbar_wait_pair<false>(&sh.dfull[0], 0, abort, peer_abort, L.err, wc);
+        if (ok0) {
+            nxt = sh.desc[0];
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&sh.dempty[0]);
+            if (job.gram_rows == 0) {
+                hc_next = L.H[nxt.rowB + et];
+                hr_next = L.H[nxt.rowA + row];
+            }
+        }
+        for (long long k = 0; k < my_units; k++) {
+            if (epi_bar_or(*abort != 0)) break;
+            const int buf = (int)(k & 1);
+            const TcUnit cur = nxt;
+            sh.hc[buf][et] = hc_next;
+            const float hr = hr_next;
+            asm volatile("bar.sync 1, %0;" ::"n"(TC_EPI_WARPS * 32) : "memory");
+            if (k + 1 < my_units) {
+                const int ds = (int)((k + 1) % TC_NDESC);
+                if (mbar_wait_pair<false>(&sh.dfull[ds], (uint32_t)(((k + 1) / TC_NDESC) & 1), abort, peer_abort, L.err, wc)) {
+                    nxt = sh.desc[ds];
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&sh.dempty[ds]);
+                    if (job.gram_rows == 0) {
+                        hc_next = L.H[nxt.rowB + et];
+                        hr_next = nxt.pad ? L.H[nxt.rowA + row] : inf;
+                    }
+                }
+            }
+            const long long ql = k * gpu + gpu - 1;
+            bool ok = mbar_wait_pair<false>(&sh.gbar[ql % TC_NGBAR], (uint32_t)((ql / TC_NGBAR) & 1), abort, peer_abort, L.err, wc);
+            ok = __all_sync(0xffffffffu, ok);
+            if (!ok) continue;
+            tc_fence_after();
+            const int J = 2 * cur.Jp + ch;
+            const bool skip = !cur.pad || ((job.gram_rows > 0) ? (J * TC_TILE >= job.gram_rows) : (J < cur.I));
+            if (skip) {
+                __syncwarp();
+                if (lane == 0) mbar_arrive_cluster(te0 + (uint32_t)(buf * 8));
+                continue;
+            }
+            const uint32_t taddr = tbase + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(buf * TC_N + ch * TC_TILE);
+            const bool diag = (J == cur.I);
+            const float *hcs = sh.hc[buf] + ch * TC_TILE;
+            SecState *st = (job.gram_rows == 0) ? &L.st[cur.sec] : nullptr;
+            for (int h = 0; h < 2; h++) {
+                uint32_t r[64];
+                tmem_ld32_nowait(taddr + (uint32_t)(h * 64), r);
+                tmem_ld32_nowait(taddr + (uint32_t)(h * 64 + 32), r + 32);
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                if (h == 1) {
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive_cluster(te0 + (uint32_t)(buf * 8));
+                }
+                if (job.gram_rows > 0) {
+                    float *o = job.gram_out + ((int64_t)cur.I * TC_TILE + row) * job.gram_rows + (int64_t)J * TC_TILE + h * 64;
+#pragma unroll
+                    for (int c = 0; c < 64; c++) o[c] = __uint_as_float(r[c]);
+                    continue;
+                }
+                screen_test_64(L, st, cur.sec, cur.I, J, row, diag, h, r, hcs, hr);
+            }
+        }
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    cluster_sync_all();                  // rank 0's MMAs and every remote arrive are complete
+    if (warp == TC_MMA_WARP) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(TC_TMEM_COLS) : "memory");
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Host side: tensor map over the operand rows and the launch.
 // ---------------------------------------------------------------------------
 
@@ -654,18 +1058,57 @@ inline cudaError_t screen_tc_prepare(int precision)
                             : cudaFuncSetAttribute(k_screen_tc<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                    TC_SMEM_BYTES);
         if (e != cudaSuccess) return e;
+        e = (precision == 2) ? cudaFuncSetAttribute(k_screen_tc2<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                    TC2_SMEM_BYTES)
+                             : cudaFuncSetAttribute(k_screen_tc2<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                    TC2_SMEM_BYTES);
+        if (e != cudaSuccess) return e;
         attr_done[fi] = true;
     }
     return cudaSuccess;
 }
 
+// CTAs of the pair form's grid: two per cluster that can be resident at
+// once (clusters need two free SMs of one GPU processing cluster).
+inline int screen_tc2_grid(int n_sm)
+{
+    static int cached = 0;
+    if (cached == 0) {
+        (void)screen_tc_prepare(1);      // the shared-memory size the query assumes
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)(n_sm & ~1));
+        cfg.blockDim = dim3(TC_THREADS);
+        cfg.dynamicSmemBytes = TC2_SMEM_BYTES;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = 2;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        int ncl = 0;
+        if (cudaOccupancyMaxActiveClusters(&ncl, k_screen_tc2<0>, &cfg) != cudaSuccess || ncl <= 0) {
+            (void)cudaGetLastError();
+            ncl = n_sm / 2;
+        }
+        cached = 2 * std::min(ncl, n_sm / 2);
+    }
+    return cached;
+}
+
 inline cudaError_t launch_screen_tc_map(const LevelDev &L, const CUtensorMap &map, int precision, int n_cta,
-                                        cudaStream_t s, TcJob job)
+                                        cudaStream_t s, TcJob job, bool pair = false)
 {
     cudaError_t e = screen_tc_prepare(precision);
     if (e != cudaSuccess) return e;
-    if (precision == 2) k_screen_tc<1><<<n_cta, TC_THREADS, TC_SMEM_BYTES, s>>>(L, map, job);
-    else k_screen_tc<0><<<n_cta, TC_THREADS, TC_SMEM_BYTES, s>>>(L, map, job);
+    if (pair) {
+        const int grid = std::max(2, n_cta & ~1);
+        if (precision == 2) k_screen_tc2<1><<<grid, TC_THREADS, TC2_SMEM_BYTES, s>>>(L, map, job);
+        else k_screen_tc2<0><<<grid, TC_THREADS, TC2_SMEM_BYTES, s>>>(L, map, job);
+    } else {
+        if (precision == 2) k_screen_tc<1><<<n_cta, TC_THREADS, TC_SMEM_BYTES, s>>>(L, map, job);
+        else k_screen_tc<0><<<n_cta, TC_THREADS, TC_SMEM_BYTES, s>>>(L, map, job);
+    }
     return cudaGetLastError();
 }
 

@@ -19,8 +19,9 @@ iteration, a different rule with its own oracle mode); profile (1: per-kernel
 CUDA-event times in stats()); wait_cycles (bound of the tensor-core screen's
 pipeline waits in clock cycles, 0 = the default of about 2 s; a wait that
 runs out makes run() raise RHSEGError with code RHSEG_ETIMEOUT); screen_group
-(K slices per tcgen05.commit of the tensor-core screen, 0 = default; chosen by
-the autotuner, results identical).
+(K slices per tcgen05.commit of the tensor-core screen, 0 = default) and
+screen_pair (1: the tensor-core screen as CTA pairs sharing 256x256 tiles),
+both chosen by the autotuner, results identical.
 """
 from __future__ import annotations
 
@@ -32,7 +33,7 @@ from . import _abi
 
 DEFAULTS = dict(rnb_levels=1, conv_nregions=1, spclust_wght=0.0, connectivity=8, min_nregions=0,
                 n_out_levels=1, seam_pass=1, precision=1, profile=0, incremental=0,
-                multi_merge=0, wait_cycles=0, screen_group=0)
+                multi_merge=0, wait_cycles=0, screen_group=0, screen_pair=0)
 
 
 class RHSEGError(RuntimeError):
@@ -200,14 +201,14 @@ def div_rn(n_hi, n_lo, d_hi, d_lo, stream=None):
     return out
 
 
-def gram_tc(X, precision=1, stream=None):
+def gram_tc(X, precision=1, stream=None, cta_pair=0):
     """G = X X^T (FP32) of 16-bit rows on the tensor cores (diagnostic of the
-    screen's contraction).  X: CUDA tensor float16/bfloat16 [rows, Bpad],
-    rows % 128 == 0, Bpad % 32 == 0."""
+    screen's contraction, in the one-CTA or the CTA-pair form).  X: CUDA
+    tensor float16/bfloat16 [rows, Bpad], rows % 128 == 0, Bpad % 32 == 0."""
     import torch
     L = _abi.load()
     X = X.contiguous()
     G = torch.empty(X.shape[0], X.shape[0], dtype=torch.float32, device=X.device)
-    _check(L.rhseg_gram_tc(C.c_void_p(X.data_ptr()), X.shape[0], X.shape[1], precision, C.c_void_p(G.data_ptr()),
+    _check(L.rhseg_gram_tc(C.c_void_p(X.data_ptr()), X.shape[0], X.shape[1], precision, int(cta_pair), C.c_void_p(G.data_ptr()),
                            _stream_ptr(stream)), "rhseg_gram_tc")
     return G

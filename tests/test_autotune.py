@@ -25,6 +25,9 @@ def test_bucket_and_key():
 def test_lookup_reads_the_stored_choice(tmp_path):
     path = str(tmp_path / "cache.json")
     assert A.lookup(224, 4096, path=path) == {}
-    json.dump({A.cache_key(224, 4096): {"screen_group": 7, "screen_ms": {"4": 1.0, "7": 0.9}}}, open(path, "w"))
-    assert A.lookup(224, 4096, path=path) == {"screen_group": 7}
+    json.dump({A.cache_key(224, 4096): {"screen_group": 7, "screen_ms": {"4": 1.0, "7": 0.9}},
+               A.cache_key(128, 1024): {"screen_pair": 1, "screen_group": 2}}, open(path, "w"))
+    assert A.lookup(224, 4096, path=path) == {"screen_group": 7, "screen_pair": 0}    # entry without a form
+    assert A.lookup(128, 1024, path=path) == {"screen_group": 2, "screen_pair": 1}
     assert A.lookup(128, 4096, path=path) == {}
+    assert A.lookup(64, 1024, path=path) == {}

@@ -181,6 +181,20 @@ def test_device_inputs_equal_host_inputs(P, orc):
     _assert_same(b, orc.run(img, mask, **kw), "device inputs")
 
 
+@pytest.mark.parametrize("precision", [1, 2])
+@pytest.mark.parametrize("si", range(len(SCENES)))
+def test_cta_pair_screen_scenes(P, orc, precision, si):
+    """The tensor-core screen as CTA pairs (screen_pair = 1): same merges as
+    the oracle on every scene (several tiles, ragged tails, odd block
+    counts, masks)."""
+    rows, cols, B, L, w, conv, conn, min_nr, n_out, seam, masked = SCENES[si]
+    img, mask = synth.make(4 if masked else 2, seed=400 + si, rows=rows, cols=cols)
+    img = np.ascontiguousarray(img[:, :, :B])
+    kw = dict(rnb_levels=L, spclust_wght=w, conv_nregions=conv, connectivity=conn, min_nregions=min_nr,
+              n_out_levels=n_out, seam_pass=seam)
+    _assert_same(_run(P, img, mask, precision=precision, screen_pair=1, **kw), orc.run(img, mask, **kw), f"scene {si}")
+
+
 def test_launch_forms_give_identical_runs(P, orc):
     """The same run through every launch form: the level's chunks replayed as
     CUDA graphs (the library's own stream, default) or launched directly (the
@@ -194,7 +208,8 @@ def test_launch_forms_give_identical_runs(P, orc):
     legacy = 1                  # cudaStreamLegacy: the legacy default stream, which cannot be captured
     torch.cuda.synchronize()
     for precision in (1, 2):
-        for extra, stream in ((dict(), None), (dict(profile=1), None), (dict(), legacy), (dict(profile=1), legacy)):
+        for extra, stream in ((dict(), None), (dict(profile=1), None), (dict(), legacy), (dict(profile=1), legacy),
+                              (dict(screen_pair=1), None), (dict(screen_pair=1, profile=1), legacy)):
             seg = P.RHSEG(img, mask, precision=precision, stream=stream, **kw, **extra)
             seg.run(stream=stream)
             _assert_same(seg, ref, f"p{precision} {extra} {'legacy' if stream is not None else 'own'} stream")

@@ -21,9 +21,14 @@ def P():
     return P
 
 
+@pytest.mark.parametrize("cta_pair", [0, 1])
 @pytest.mark.parametrize("precision", [1, 2])
-@pytest.mark.parametrize("rows,bpad", [(128, 64), (256, 128), (384, 256), (128, 448), (256, 224), (128, 32), (256, 96)])
-def test_gram_matches_exact_product(P, precision, rows, bpad):
+@pytest.mark.parametrize("rows,bpad", [(128, 64), (256, 128), (384, 256), (128, 448), (256, 224), (128, 32), (256, 96),
+                                       (640, 224)])
+def test_gram_matches_exact_product(P, precision, rows, bpad, cta_pair):
+    """One-CTA form and CTA-pair form (two CTAs share each 256x256 tile; a
+    wrong operand split or column order shows as errors of the size of the
+    entries)."""
     import torch
     rng = np.random.default_rng(rows * 7 + bpad + precision)
     X = rng.normal(0, 1000, (rows, bpad))
@@ -31,7 +36,7 @@ def test_gram_matches_exact_product(P, precision, rows, bpad):
     X[rng.random(rows) < 0.1] *= 1e-3            # mixed magnitudes
     dt = torch.float16 if precision == 1 else torch.bfloat16
     Xt = torch.tensor(X, dtype=dt, device="cuda")
-    G = P.gram_tc(Xt, precision=precision).cpu().numpy().astype(np.float64)
+    G = P.gram_tc(Xt, precision=precision, cta_pair=cta_pair).cpu().numpy().astype(np.float64)
     Xq = Xt.float().cpu().numpy().astype(np.float64)          # the values the tensor cores saw
     exact = Xq @ Xq.T                                           # products and sums exact in float64 here
     absum = np.abs(Xq) @ np.abs(Xq).T
@@ -51,6 +56,8 @@ def test_gram_rejects_bad_shapes(P):
         P.gram_tc(torch.zeros(128, 40, dtype=torch.float16, device="cuda"))
     with pytest.raises(P.RHSEGError):
         P.gram_tc(torch.zeros(128, 48, dtype=torch.float16, device="cuda"))
+    with pytest.raises(P.RHSEGError):
+        P.gram_tc(torch.zeros(128, 64, dtype=torch.float16, device="cuda"), cta_pair=2)
 
 
 @pytest.mark.parametrize("precision", [1, 2])
