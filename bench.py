@@ -31,6 +31,14 @@ sys.path.insert(0, ROOT)
 METRIC = "region-pair dissimilarities/s and RHSEG end-to-end s at 1024²×224, mixed vs FP64, label-exact"
 UNIT = "pairs/s"
 
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum, ncu, cold L2) per
+# pair covered by the tcgen05 screen's MMAs, summed over every screen launch of
+# the deepest level of the 512x512x224 crop (64 sections of 64x64 pixels,
+# the size of the 1024x1024x224 run's deepest sections) and divided by that
+# level's covered pairs (stats level_screen_evaluated); keyed by (bands,
+# screen_pair).  The screen reads the operand rows of the units it keeps, so
+# its traffic follows the covered pairs.
+SCREEN_DRAM_BYTES_PER_COVERED_PAIR = {}
 PEAKS_FALLBACK = {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "bf16_tflops_sustained": 1400.0, "sm_max_mhz": 2032.0}
 
 
@@ -336,8 +344,14 @@ def main():
     else:
         bound, peak = "alu", 148 * 128 * 2.0 * float(peaks.get("sm_max_mhz", 2032.0)) / 1e6
         peak_note = "fp32 FMA: 148 SM x 128 lanes x 2 flop x max SM clock"
+    traffic, traffic_basis = None, "no ncu capture of this screen form and band count"
+    bpp = SCREEN_DRAM_BYTES_PER_COVERED_PAIR.get((B, int(params.get("screen_pair", 0))))
+    if impl == 3 and bpp is not None and scr_n > 0 and scr_eval > 0:
+        traffic = bpp * scr_eval / scr_n
+        traffic_basis = (f"{bpp:.4g} DRAM bytes per covered pair (ncu, every deepest-level screen launch of the "
+                         f"512x512x224 crop, same section size) x this run's covered pairs per launch")
     roofline = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak if peak else None, "traffic": None,
+                "frac": achieved / peak if peak else None, "traffic": traffic, "traffic_basis": traffic_basis,
                 "kernel": {1: "screen_simt<f64>", 2: "screen_simt<f32 accumulate>",
                            3: "screen_tcgen05_cta_pair" if params.get("screen_pair") else "screen_tcgen05"}.get(impl, "none"),
                 "launches": scr_n, "avg_launch_ms": scr_ms / max(scr_n, 1),
@@ -376,6 +390,8 @@ def main():
         "level_iters": stats[-1]["level_iters"][:params["rnb_levels"]],
         "level_kernel_ms": {k: [round(x, 1) for x in stats[-1]["level_" + k + "_ms"][:params["rnb_levels"]]]
                             for k in ("screen", "adj", "spec")},
+        "level_screen_evaluated": stats[-1]["level_screen_evaluated"][:params["rnb_levels"]],
+        "level_screen_launches": stats[-1]["level_iters"][:params["rnb_levels"]] if params["spclust_wght"] > 0 else None,
     }
 
     if not args.no_e2e:

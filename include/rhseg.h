@@ -170,6 +170,8 @@ typedef struct rhseg_stats {
     double  screen_err_bound_max; /* max |K~ - K| / bound over the same pairs: the
                                      screen's error model holds iff this is <= 1    */
     int64_t screen_err_pairs;     /* re-checked pairs the two maxima cover         */
+    int64_t level_screen_evaluated[6];  /* per level (index level-1) split of
+                                           screen_evaluated                    */
 } rhseg_stats;
 
 typedef struct rhseg_handle rhseg_handle;

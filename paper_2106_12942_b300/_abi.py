@@ -48,6 +48,7 @@ class Stats(C.Structure):
         ("level_screen_ms", C.c_double * 6), ("level_adj_ms", C.c_double * 6), ("level_spec_ms", C.c_double * 6),
         ("screen_evaluated", C.c_int64), ("device_allocs", C.c_int64),
         ("screen_err_rel_max", C.c_double), ("screen_err_bound_max", C.c_double), ("screen_err_pairs", C.c_int64),
+        ("level_screen_evaluated", C.c_int64 * 6),
     ]
 
 

@@ -845,7 +845,8 @@ static int run_impl(rhseg_handle *h)
         if (inc)
             if ((rc = h->ckey.alloc((size_t)G.nsec * cand_cap))) return rc;
         const bool skip_units = h->nlo.p != nullptr && h->p.spclust_wght > 0.0;
-        const int32_t ucap = (int32_t)tc_section_units(m0max) + 1;
+        // the pair form lists two words per pair, at most one pair per unit
+        const int32_t ucap = ((int32_t)tc_section_units(m0max) + 1) * (h->p.screen_pair ? 2 : 1);
         if (skip_units)
             if ((rc = h->ulist.alloc((size_t)G.nsec * ucap))) return rc;
         CK(cudaMemcpyAsync(h->aoff.p, aoff.data(), 8 * (G.nsec + 1), cudaMemcpyHostToDevice, s));
@@ -1051,6 +1052,7 @@ static int run_impl(rhseg_handle *h)
             h->stats.iterations += q.iter;
             h->stats.screened_pairs += q.screened;
             h->stats.screen_evaluated += q.evaluated;
+            h->stats.level_screen_evaluated[lev - 1] += q.evaluated;
             h->stats.candidates += q.cands;
             h->stats.candidates_below += q.cands_true;
             h->stats.fallbacks += q.fallbacks;

@@ -95,7 +95,7 @@ struct LevelDev {
     int32_t *err;              // device error word
     long long wait_cycles;     // bound of the screen's pipeline waits (0: the default)
     int32_t tc_group;          // K slices per tcgen05.commit of the screen (0: the default)
-    int32_t tc_pair;           // 1: the screen runs as CTA pairs; ulist then lists 256x256 tiles
+    int32_t tc_pair;           // 1: the screen runs as CTA pairs; ulist then lists unit pairs
     int32_t *wlist;            // [nsec] sections whose positions were rebuilt this iteration
     int32_t *wcount;           // their number
     // incremental spectral minima (null unless that mode is on)
@@ -112,7 +112,7 @@ struct LevelDev {
     float *brng;               // per 128-position block x 4: kept (min nlo, max nhi, max sk), exact at a
                                // rebuild and widened by every merge since (tensor-core screen)
     int32_t *ulist;            // [nsec][ucap] kept units of the step, (I << 16) | Jp; with tc_pair
-                               // kept tiles, (Ip << 16) | (Jp << 2) | (bit h: half I = 2 Ip + h kept)
+                               // pairs of kept units of one column block Jp: (I0 << 16) | Jp, I1 (-1: none)
     int32_t ucap;
     unsigned long long *sortk; // per slot x 2: scratch of the norm-order sort of the positions
     float inc_onepg;           // 1 + gamma_B for a binary32 sum of Bpad non-negative terms (rounded up)

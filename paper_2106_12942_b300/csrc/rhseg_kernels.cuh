@@ -1172,32 +1172,81 @@ __device__ void block_unit_list(const LevelDev &L, int sec, SecState &st, float 
         }
         return false;
     };
+    int32_t *ul = L.ulist + (int64_t)sec * L.ucap;
+    if (L.tc_pair) {
+        // CTA-pair form: the kept units of each column block Jp, in
+        // increasing I, paired two by two into (I0, I1) (an odd last unit
+        // with I1 = -1), listed column by column as two words,
+        // (I0 << 16) | Jp and I1.  A pair shares the B block Jp, so the two
+        // CTAs of a cluster can run it as one M = 256 MMA.
+        __shared__ int32_t pbase[UL_MAX_BLOCKS / 2 + 1];
+        int npairs;
+        if (ranges) {
+            for (int Jp = wid; Jp < nbp; Jp += nw) {             // pairs per column
+                const int ni = min(2 * Jp + 2, nb);
+                int c = 0;
+                for (int i0 = 0; i0 < ni; i0 += 32) {
+                    const int I = i0 + lane;
+                    c += __popc(__ballot_sync(0xffffffffu, I < ni && unit_kept(I, Jp)));
+                }
+                if (lane == 0) pbase[Jp] = (c + 1) >> 1;
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) {                              // exclusive prefix (nbp <= 256)
+                int acc = 0;
+                for (int j = 0; j < nbp; j++) { const int v = pbase[j]; pbase[j] = acc; acc += v; }
+                pbase[nbp] = acc;
+            }
+            __syncthreads();
+            for (int Jp = wid; Jp < nbp; Jp += nw) {
+                const int ni = min(2 * Jp + 2, nb);
+                const int64_t b0 = pbase[Jp];
+                int c = 0;
+                for (int i0 = 0; i0 < ni; i0 += 32) {
+                    const int I = i0 + lane;
+                    const bool k = I < ni && unit_kept(I, Jp);
+                    const unsigned m = __ballot_sync(0xffffffffu, k);
+                    if (k) {
+                        const int r = c + __popc(m & ((1u << lane) - 1u));
+                        const int64_t e = 2 * (b0 + (r >> 1));
+                        if (r & 1) ul[e + 1] = I;
+                        else ul[e] = (I << 16) | Jp;
+                    }
+                    c += __popc(m);
+                }
+                if ((c & 1) && lane == 0) ul[2 * (b0 + (c >> 1)) + 1] = -1;
+            }
+            npairs = pbase[nbp];
+        } else {
+            // every unit kept: the two halves of each tile (Ip, Jp), Ip <= Jp
+            npairs = nbp * (nbp + 1) / 2;
+            for (int t = threadIdx.x; t < npairs; t += blockDim.x) {
+                int Ip, Jp;
+                tri_decode(t, nbp, Ip, Jp);
+                ul[2 * (int64_t)t] = ((2 * Ip) << 16) | Jp;
+                ul[2 * (int64_t)t + 1] = (2 * Ip + 1 < nb) ? 2 * Ip + 1 : -1;
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            st.ranges_stale = 0;
+            st.nunits = npairs;
+            st.evaluated += (int64_t)npairs * 256 * 256;
+        }
+        return;
+    }
     // one-CTA form: units (I, Jp) with 2 Jp + 1 >= I (the two 128-row halves
     // of every upper-triangle tile of 256-row blocks), listed row block by
-    // row block (I, then Jp).  CTA-pair form: tiles (Ip, Jp), Ip <= Jp, with
-    // at least one kept half, listed by Ip, then Jp
-    const bool pair = L.tc_pair != 0;
-    int32_t *ul = L.ulist + (int64_t)sec * L.ucap;
-    const int nall = pair ? nbp * nbp : nb * nbp;
+    // row block (I, then Jp)
+    const int nall = nb * nbp;
     for (int t0 = 0; t0 < nall; t0 += blockDim.x) {
         const int t = t0 + threadIdx.x;
         int keep = 0, entry = 0;
         if (t < nall) {
-            if (pair) {
-                const int Ip = t / nbp, Jp = t - Ip * nbp;
-                if (Ip <= Jp) {
-                    int mask = 0;
-                    for (int hh = 0; hh < 2; hh++)
-                        if (2 * Ip + hh < nb && unit_kept(2 * Ip + hh, Jp)) mask |= 1 << hh;
-                    keep = mask != 0;
-                    entry = (Ip << 16) | (Jp << 2) | mask;
-                }
-            } else {
-                const int I = t / nbp, Jp = t - I * nbp;
-                if (2 * Jp + 1 >= I) {
-                    keep = unit_kept(I, Jp) ? 1 : 0;
-                    entry = (I << 16) | Jp;
-                }
+            const int I = t / nbp, Jp = t - I * nbp;
+            if (2 * Jp + 1 >= I) {
+                keep = unit_kept(I, Jp) ? 1 : 0;
+                entry = (I << 16) | Jp;
             }
         }
         int incl = keep;
@@ -1218,7 +1267,7 @@ __device__ void block_unit_list(const LevelDev &L, int sec, SecState &st, float 
     if (threadIdx.x == 0) {
         st.ranges_stale = 0;
         st.nunits = base;
-        st.evaluated += (int64_t)base * (pair ? 256 * 256 : 128 * 256);
+        st.evaluated += (int64_t)base * 128 * 256;
     }
 }
 

@@ -724,18 +724,18 @@ __device__ __forceinline__ void tc2_commit(uint64_t *bar, uint16_t mask)
         : "memory");
 }
 
-// Pair unit t of this launch: tile (Ip, Jp); this CTA (rank r) takes A
-// block I = 2 Ip + r.  u.pad = 1 when this half is listed (screen mode:
-// the half may hold a pair below the threshold; Gram mode: the block lies
-// inside the rows).  u.rowB is the first row of the whole 256-row block.
+// Pair unit t of this launch: A blocks (I0, I1) against the 256-row block
+// Jp; this CTA (rank r) takes I_r.  u.pad = 1 when this CTA's block is real
+// (screen mode: I1 = -1 pads an odd column with a copy of I0, whose
+// results are not tested; Gram mode: the block lies inside the rows).
+// u.rowB is the first row of the whole 256-row block.
 __device__ __forceinline__ void tc2_unit(const TcShared2 &sh, const TcJob &job, long long t, int &cursor,
                                          uint32_t rank, TcUnit &u, const int32_t *ulist, int ucap)
 {
-    int Ip;
     if (job.gram_rows > 0) {
         const int nbp = (job.gram_rows + TC_N - 1) / TC_N;
         u.sec = 0;
-        Ip = (int)(t / nbp);
+        const int Ip = (int)(t / nbp);
         u.Jp = (int)(t % nbp);
         u.I = 2 * Ip + (int)rank;
         u.pad = (u.I * TC_TILE < job.gram_rows) ? 1 : 0;
@@ -747,11 +747,11 @@ __device__ __forceinline__ void tc2_unit(const TcShared2 &sh, const TcJob &job, 
     while (sh.pre[s + 1] <= t) s++;
     cursor = s;
     u.sec = s;
-    const int32_t e = ulist[(int64_t)s * ucap + (t - sh.pre[s])];
-    Ip = e >> 16;
-    u.Jp = (e >> 2) & 0x3fff;
-    u.I = 2 * Ip + (int)rank;
-    u.pad = (e >> rank) & 1;
+    const int32_t *e = ulist + (int64_t)s * ucap + 2 * (t - sh.pre[s]);
+    const int32_t e0 = e[0], e1 = e[1];
+    u.Jp = e0 & 0xffff;
+    u.I = (rank == 0 || e1 < 0) ? (e0 >> 16) : e1;
+    u.pad = (rank == 0 || e1 >= 0) ? 1 : 0;
     u.rowA = sh.spoff[s] + (int64_t)u.I * TC_TILE;
     u.rowB = sh.spoff[s] + (int64_t)u.Jp * TC_N;
 }
