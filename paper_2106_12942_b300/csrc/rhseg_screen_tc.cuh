@@ -52,6 +52,7 @@ constexpr int TC_MMA_WARP = TC_PROD_WARPS;
 constexpr int TC_EPI_WARP0 = TC_PROD_WARPS + 1;
 constexpr int TC_THREADS = 32 * (TC_PROD_WARPS + 1 + TC_EPI_WARPS);
 static_assert(TC_STAGES % TC_PROD_WARPS == 0, "each producer owns whole ring slots");
+static_assert((TC_STAGES & (TC_STAGES - 1)) == 0, "ring slot by mask");
 constexpr uint32_t TC_TMEM_COLS = 2 * TC_N;
 constexpr long long TC_WAIT_CYCLES = 4000000000ll;           // default wait bound: about 2 s at 2 GHz
 
@@ -128,6 +129,7 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort, int32_t *err,
                                           long long cycles)
 {
+    if (mbar_try_wait(bar, parity)) return true;     // the usual case: no clock read
     long long t0 = clock64();
     while (!mbar_try_wait(bar, parity)) {
         if (*abort) return false;
@@ -435,10 +437,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_screen_tc(LevelDev L, const _
             long long kdec = -1;
             TcUnit u{};
             const long long nslices = my_units * natoms;
+            long long k = p / natoms;                        // unit and K slice of slice c
+            int kc = p - (int)k * natoms;
             for (long long c = p; c < nslices && !*abort; c += TC_PROD_WARPS) {
-                const long long k = c / natoms;
-                const int kc = (int)(c - k * natoms);
-                const int slot = (int)(c % TC_STAGES);
+                const int slot = (int)(c & (TC_STAGES - 1));
                 if (k != kdec) {
                     tc_unit(sh, job, blockIdx.x + k * gridDim.x, total, cursor, u, job.gram_rows > 0 ? nullptr : L.ulist,
                             L.ucap);
@@ -462,6 +464,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_screen_tc(LevelDev L, const _
                 tma_load_2d(b + TC_A_BYTES, &tmap, x, (int)u.rowB + TC_TILE, &sh.full[slot], pol);
                 sh.slot_q[slot] = k * gpu + kc / G;
                 sh.slot_fills[slot]++;
+                kc += TC_PROD_WARPS;
+                while (kc >= natoms) { kc -= natoms; k++; }
             }
             // every load this producer issued has landed before the CTA may
             // exit (immediate unless the CTA aborted with copies in flight)
@@ -483,6 +487,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_screen_tc(LevelDev L, const _
                 tc_fence_after();
                 const uint32_t dt = tbase + (uint32_t)(buf * TC_N);
                 bool ok = true;
+                int ing = 0;                                 // K slices in the open commit group
                 for (int kc = 0; kc < natoms; kc++) {
                     if (!mbar_wait(&sh.full[slot], phase, abort, L.err, wc)) { ok = false; break; }
                     tc_fence_after();
@@ -493,9 +498,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_screen_tc(LevelDev L, const _
                         tc_mma(dt, ad + (uint64_t)(2 * kk), bd + (uint64_t)(2 * kk), idesc, (kc > 0 || kk > 0) ? 1u : 0u);
                     issued = true;
                     if (++slot == TC_STAGES) { slot = 0; phase ^= 1; }
-                    if ((kc + 1) % G == 0 || kc + 1 == natoms) {
+                    if (++ing == G || kc + 1 == natoms) {
                         tc_commit(&sh.gbar[q % TC_NGBAR]);          // releases the group's slots; the
                         q++;                                         // unit's last group also readies D
+                        ing = 0;
                     }
                 }
                 if (!ok) break;
@@ -606,13 +612,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_screen_tc(LevelDev L, const _
 // CTAs' shared memory and write each CTA's 128x256 accumulator into its own
 // tensor memory.  Per K slice a CTA loads 16 KB instead of 24 KB, so the
 // same shared memory holds a 12-slot ring: 1.5x the MMA work in flight for
-// the same bytes.  The peer's slices are reported to rank 0 by the peer's
-// MMA warp (it waits on its own transaction barrier, then arrives on rank
-// 0's barrier), so every TMA copy completes on a barrier of the CTA it
-// writes to and each CTA can wait for its own copies before leaving.
-// Commit groups arrive on both CTAs' barriers (multicast); rank 0's MMAs
-// wait until both epilogues have read an accumulator buffer.  Epilogue and
-// test are those of the one-CTA form, per CTA.
+// the same bytes.  Both CTAs' TMA copies of a K slice complete on rank 0's
+// barrier for that slot (the peer's copies with the cta_group::2 form of
+// the TMA load; rank 0 expects the bytes of both), so rank 0's MMAs start
+// as soon as the slice is whole.  Before leaving, rank 0 balances any slot
+// that only one CTA refilled (an aborted launch) and waits until every
+// copy into either CTA has landed.  Commit groups arrive on both CTAs'
+// barriers (multicast); rank 0's MMAs wait until both epilogues have read
+// an accumulator buffer.  Epilogue and test are those of the one-CTA form,
+// per CTA.
 // ---------------------------------------------------------------------------
 constexpr int TC2_BH_BYTES = TC_TILE * TC_KATOM * 2;            // 8 KB: this CTA's 128 rows of the B block
 constexpr int TC2_STAGE_BYTES = TC_A_BYTES + TC2_BH_BYTES;      // 16 KB per K slice and CTA
@@ -620,8 +628,7 @@ constexpr int TC2_STAGES = 12;
 static_assert(TC2_STAGES % TC_PROD_WARPS == 0, "each producer owns whole ring slots");
 
 struct TcShared2 {
-    uint64_t full[TC2_STAGES];                // this CTA's K slice landed (TMA transaction count)
-    uint64_t pfull[TC2_STAGES];               // rank 0: the peer's K slice landed (relayed)
+    uint64_t full[TC2_STAGES];                // rank 0: both CTAs' K slice landed (TMA transaction count)
     uint64_t gbar[TC_NGBAR];                  // MMAs of a group of K slices complete (both CTAs)
     uint64_t tempty[2];                       // rank 0: accumulator buffer read out by both epilogues
     uint64_t dfull[TC_NDESC], dempty[TC_NDESC];
@@ -630,6 +637,7 @@ struct TcShared2 {
     int abort;
     long long slot_q[TC2_STAGES];
     int slot_fills[TC2_STAGES];
+    int peer_fills[TC2_STAGES];               // rank 0: loads the peer issued into each slot (written at the end)
     TcUnit desc[TC_NDESC];
     alignas(16) float hc[2][TC_N];
     long long pre[MAX_SECTIONS + 1];
@@ -696,6 +704,23 @@ __device__ __forceinline__ bool mbar_wait_pair(uint64_t *bar, uint32_t parity, v
         }
     }
     return true;
+}
+
+// TMA load into this CTA's shared memory whose completion (bytes) is
+// reported on a barrier of either CTA of the pair (`cl_bar`: a shared::cluster
+// address, here rank 0's).
+__device__ __forceinline__ void tma_load_2d_pair(void *dst, const CUtensorMap *map, int x, int y, uint32_t cl_bar,
+                                                 uint64_t policy)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.cta_group::2.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], "
+        "[%1, {%2, %3}], [%4], %5;" ::"r"(smem_u32(dst)),
+        "l"((uint64_t)map), "r"(x), "r"(y), "r"(cl_bar), "l"(policy)
+        : "memory");
+}
+__device__ __forceinline__ void mbar_complete_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.complete_tx.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
 }
 
 // Instruction descriptor of the pair's MMA: kind::f16, FP32 accumulator,
@@ -796,9 +821,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(TC_THREADS, 1)
     if (threadIdx.x == 0) {
         for (int s = 0; s < TC2_STAGES; s++) {
             mbar_init(&sh.full[s], 1);
-            mbar_init(&sh.pfull[s], 1);
             sh.slot_q[s] = -1;
             sh.slot_fills[s] = 0;
+            sh.peer_fills[s] = 0;
         }
         for (int g = 0; g < TC_NGBAR; g++) mbar_init(&sh.gbar[g], 1);
         for (int b = 0; b < 2; b++) mbar_init(&sh.tempty[b], 2 * TC_EPI_WARPS);
@@ -830,11 +855,12 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(TC_THREADS, 1)
             int cursor = cursor0;
             long long kdec = -1;
             TcUnit u{};
+            const uint32_t full0 = mapa_shared(smem_u32(&sh.full[0]), 0u);     // rank 0's slot barriers
             const long long nslices = my_units * natoms;
+            long long k = p / natoms;                        // unit and K slice of slice c
+            int kc = p - (int)k * natoms;
+            int slot = p;
             for (long long c = p; c < nslices && !*abort; c += TC_PROD_WARPS) {
-                const long long k = c / natoms;
-                const int kc = (int)(c - k * natoms);
-                const int slot = (int)(c % TC2_STAGES);
                 if (k != kdec) {
                     tc2_unit(sh, job, cid + k * ncl, cursor, rank, u, L.ulist, L.ucap);
                     kdec = k;
@@ -853,14 +879,28 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(TC_THREADS, 1)
                     break;
                 uint8_t *a = ring + slot * TC2_STAGE_BYTES;                      // A slice, then the B half
                 const int x = kc * TC_KATOM;
-                mbar_expect_tx(&sh.full[slot], (uint32_t)TC2_STAGE_BYTES);
-                tma_load_2d(a, &tmap, x, (int)u.rowA, &sh.full[slot], pol);
-                tma_load_2d(a + TC_A_BYTES, &tmap, x, (int)(u.rowB + (int64_t)rank * TC_TILE), &sh.full[slot], pol);
+                if (rank == 0) {
+                    mbar_expect_tx(&sh.full[slot], (uint32_t)(2 * TC2_STAGE_BYTES));    // both CTAs' bytes
+                    tma_load_2d(a, &tmap, x, (int)u.rowA, &sh.full[slot], pol);
+                    tma_load_2d(a + TC_A_BYTES, &tmap, x, (int)u.rowB, &sh.full[slot], pol);
+                } else {
+                    const uint32_t fb = full0 + (uint32_t)(slot * 8);
+                    tma_load_2d_pair(a, &tmap, x, (int)u.rowA, fb, pol);
+                    tma_load_2d_pair(a + TC_A_BYTES, &tmap, x, (int)(u.rowB + TC_TILE), fb, pol);
+                }
                 sh.slot_q[slot] = k * gpu + kc / G;
                 sh.slot_fills[slot]++;
+                kc += TC_PROD_WARPS;
+                while (kc >= natoms) { kc -= natoms; k++; }
+                slot += TC_PROD_WARPS;
+                if (slot >= TC2_STAGES) slot -= TC2_STAGES;
             }
-            for (int sl = p; sl < TC2_STAGES; sl += TC_PROD_WARPS)
-                if (sh.slot_fills[sl] > 0) mbar_wait_landed(&sh.full[sl], (uint32_t)((sh.slot_fills[sl] - 1) & 1), L.err);
+            // the peer's loads per slot, for rank 0's balance at the end
+            if (rank == 1) {
+                const uint32_t pf0 = mapa_shared(smem_u32(&sh.peer_fills[0]), 0u);
+                for (int sl = p; sl < TC2_STAGES; sl += TC_PROD_WARPS)
+                    st_cluster_u32(pf0 + (uint32_t)(sl * 4), (uint32_t)sh.slot_fills[sl]);
+            }
         }
         __syncwarp();
     } else if (warp == TC_MMA_WARP) {
@@ -879,8 +919,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(TC_THREADS, 1)
                 const uint32_t dt = tbase + (uint32_t)(buf * TC_N);
                 bool ok = true;
                 for (int kc = 0; kc < natoms; kc++) {
-                    if (!mbar_wait_pair<false>(&sh.full[slot], phase, abort, peer_abort, L.err, wc) ||
-                        !mbar_wait_pair<true>(&sh.pfull[slot], phase, abort, peer_abort, L.err, wc)) {
+                    if (!mbar_wait_pair<true>(&sh.full[slot], phase, abort, peer_abort, L.err, wc)) {
                         ok = false;
                         break;
                     }
@@ -902,17 +941,6 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(TC_THREADS, 1)
             if (*abort && issued) {
                 tc2_commit(&sh.drain, (uint16_t)0x1);
                 mbar_wait_landed(&sh.drain, 0, L.err);
-            }
-        } else if (lane == 0) {
-            // ---------------- relay (rank 1): this CTA's slices to rank 0 ----------------
-            const uint32_t pf0 = mapa_shared(smem_u32(&sh.pfull[0]), 0u);
-            int slot = 0;
-            uint32_t phase = 0;
-            const long long nslices = my_units * natoms;
-            for (long long c = 0; c < nslices && !*abort; c++) {
-                if (!mbar_wait_pair<false>(&sh.full[slot], phase, abort, peer_abort, L.err, wc)) break;
-                mbar_arrive_cluster(pf0 + (uint32_t)(slot * 8));
-                if (++slot == TC2_STAGES) { slot = 0; phase ^= 1; }
             }
         }
         __syncwarp();
@@ -994,7 +1022,24 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(TC_THREADS, 1)
 
     tc_fence_before();
     __syncthreads();
-    cluster_sync_all();                  // rank 0's MMAs and every remote arrive are complete
+    cluster_sync_all();                  // both CTAs stopped issuing; the peer's load counts are in place
+    // Every copy into either CTA completes on rank 0's slot barriers.  A
+    // slot refilled by one CTA only (a launch that stopped early) is
+    // balanced first: the missing CTA's bytes are marked done, or rank 0's
+    // arrival is added; then rank 0 waits for each slot's last phase.  The
+    // two counts differ by at most one (a slot is refilled only after both
+    // CTAs' previous loads into it were consumed).
+    if (rank == 0 && warp < TC_PROD_WARPS && lane == 0) {
+        for (int sl = warp; sl < TC2_STAGES; sl += TC_PROD_WARPS) {
+            const int lf = sh.slot_fills[sl], pf = sh.peer_fills[sl];
+            if (lf == pf + 1) mbar_complete_tx(&sh.full[sl], (uint32_t)TC2_STAGE_BYTES);
+            else if (pf == lf + 1) mbar_expect_tx(&sh.full[sl], (uint32_t)TC2_STAGE_BYTES);
+            const int nf = max(lf, pf);
+            if (nf > 0) mbar_wait_landed(&sh.full[sl], (uint32_t)((nf - 1) & 1), L.err);
+        }
+    }
+    __syncthreads();
+    cluster_sync_all();                  // rank 0's MMAs, every copy and every remote arrive are complete
     if (warp == TC_MMA_WARP) {
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(TC_TMEM_COLS) : "memory");
