@@ -39,7 +39,7 @@ UNIT = "pairs/s"
 # screen_pair).  The screen reads the operand rows of the units it keeps, so
 # its traffic follows the covered pairs.
 SCREEN_DRAM_BYTES_PER_COVERED_PAIR = {
-    # one-CTA form, 16-bit operands: 210.49 GB over the 3,657 deepest-level launches of the crop,
+    # one-CTA form, 16-bit operands: 210.50 GB over the 3,657 deepest-level launches of the crop,
     # whose covered pairs were 2.1223e11
     (224, 0): 0.9918,
 }
