@@ -112,6 +112,14 @@ typedef struct rhseg_params {
                               M = 256: each CTA loads 16 KB per K slice instead of 24 KB);
                               0 = one CTA per 128x256 unit.  Results identical; a
                               schedule choice of the autotuner */
+    int32_t adjacency;     /* region adjacency of a section (Section 4.1): 0 = dense bit
+                              matrix, m0^2 / 8 bytes for m0 regions at the level start
+                              (default); 1 = sorted neighbour lists in a per-section pool,
+                              memory in proportion to the region edges (at most 10 words per
+                              directed pixel edge, build scratch included), for large
+                              sections.  Results identical.  Not with incremental = 1
+                              (RHSEG_EINVAL) */
+    int32_t reserved;      /* set to 0 */
 } rhseg_params;
 
 /* One merge-log record.  kind 0 = adjacent merge, 1 = spectral merge,
@@ -172,6 +180,9 @@ typedef struct rhseg_stats {
     int64_t screen_err_pairs;     /* re-checked pairs the two maxima cover         */
     int64_t level_screen_evaluated[6];  /* per level (index level-1) split of
                                            screen_evaluated                    */
+    int64_t adjacency_bytes;  /* largest device memory the region adjacency of one
+                                 level took in the last rhseg_run (bit matrices, or
+                                 lists, offsets and their build scratch)           */
 } rhseg_stats;
 
 typedef struct rhseg_handle rhseg_handle;

@@ -21,7 +21,7 @@ class Params(C.Structure):
         ("connectivity", C.c_int32), ("min_nregions", C.c_int32), ("n_out_levels", C.c_int32),
         ("seam_pass", C.c_int32), ("precision", C.c_int32), ("profile", C.c_int32), ("incremental", C.c_int32),
         ("multi_merge", C.c_int32), ("wait_cycles", C.c_int64), ("screen_group", C.c_int32),
-        ("screen_pair", C.c_int32),
+        ("screen_pair", C.c_int32), ("adjacency", C.c_int32), ("reserved", C.c_int32),
     ]
 
 
@@ -48,7 +48,7 @@ class Stats(C.Structure):
         ("level_screen_ms", C.c_double * 6), ("level_adj_ms", C.c_double * 6), ("level_spec_ms", C.c_double * 6),
         ("screen_evaluated", C.c_int64), ("device_allocs", C.c_int64),
         ("screen_err_rel_max", C.c_double), ("screen_err_bound_max", C.c_double), ("screen_err_pairs", C.c_int64),
-        ("level_screen_evaluated", C.c_int64 * 6),
+        ("level_screen_evaluated", C.c_int64 * 6), ("adjacency_bytes", C.c_int64),
     ]
 
 

@@ -173,6 +173,11 @@ struct rhseg_handle {
     DBuf<uint32_t> mP;
     // per level, sized at run time
     DBuf<uint32_t> adj;
+    // CSR adjacency (params.adjacency = 1): pools, per-slot offsets and
+    // lengths, the sort buffer of the build and per-section layout
+    DBuf<int32_t> nbr, nofs, ndeg;
+    DBuf<unsigned long long> ckeys, ccnt;
+    DBuf<int64_t> cebase, cepow, cpbase, chcap;
     DBuf<int64_t> aoff;
     DBuf<int32_t> Wrow, ref;
     DBuf<uint32_t> cand;
@@ -219,6 +224,8 @@ static int check_params(const rhseg_params *p, int32_t rows, int32_t cols, int32
     if (p->wait_cycles < 0) return RHSEG_EINVAL;
     if (p->screen_group < 0 || p->screen_group > 8) return RHSEG_EINVAL;
     if (p->screen_pair < 0 || p->screen_pair > 1) return RHSEG_EINVAL;
+    if (p->adjacency < 0 || p->adjacency > 1) return RHSEG_EINVAL;
+    if (p->adjacency && p->incremental) return RHSEG_EINVAL;   // the incremental kernels read the bit matrix
     return RHSEG_OK;
 }
 
@@ -490,6 +497,15 @@ static int common_create(rhseg_handle *h, const rhseg_params *p, void *stream)
     if ((rc = h->log.alloc(h->log_cap))) return rc;
     if ((rc = h->err.alloc(1))) return rc;
     if ((rc = h->wlist.alloc(nsec_max))) return rc;
+    if (p->adjacency) {
+        if ((rc = h->nofs.alloc(P))) return rc;
+        if ((rc = h->ndeg.alloc(P))) return rc;
+        if ((rc = h->ccnt.alloc(nsec_max))) return rc;
+        if ((rc = h->cebase.alloc(nsec_max + 1))) return rc;
+        if ((rc = h->cepow.alloc(nsec_max))) return rc;
+        if ((rc = h->cpbase.alloc(nsec_max + 1))) return rc;
+        if ((rc = h->chcap.alloc(nsec_max))) return rc;
+    }
     if ((rc = h->wcount.alloc(1))) return rc;
     CK(cudaMemset(h->wcount.p, 0, 4));
     if ((rc = h->active.alloc(2))) return rc;
@@ -828,6 +844,7 @@ static int run_impl(rhseg_handle *h)
             m0max = std::max(m0max, m0);
             W[k] = ((ceil_div(m0, 32) + 3) / 4) * 4;
             if (W[k] == 0) W[k] = 4;
+            if (h->p.adjacency) W[k] = 0;              // lists instead of the bit matrix
             aoff[k] = atot;
             atot += (int64_t)m0 * W[k];
             maxpairs = std::max(maxpairs, (int64_t)m0 * (m0 - 1) / 2);
@@ -856,8 +873,51 @@ static int run_impl(rhseg_handle *h)
                                                   T.S.p, T.n.p, T.rid.p, T.alive.p, T.parent.p, T.absorbed_at.p,
                                                   T.bestK.p, T.bestP.p); h->nlaunch++;
         k_init_parent<<<dim3(8, G.nsec), 256, 0, s>>>(T.parent.p, GJ[0].p, h->st.p, G.nsec); h->nlaunch++;
-        k_build_adj<<<grid_pix, 256, 0, s>>>(g, h->label.p, h->slot_of_id.p, GI[1].p, GI[2].p, lev - 1,
-                                             h->p.connectivity, GJ[0].p, h->aoff.p, h->Wrow.p, h->adj.p); h->nlaunch++;
+        const bool csr = h->p.adjacency != 0;
+        if (!csr) {
+            k_build_adj<<<grid_pix, 256, 0, s>>>(g, h->label.p, h->slot_of_id.p, GI[1].p, GI[2].p, lev - 1,
+                                                 h->p.connectivity, GJ[0].p, h->aoff.p, h->Wrow.p, h->adj.p);
+            h->nlaunch++;
+            h->stats.adjacency_bytes = std::max<int64_t>(h->stats.adjacency_bytes, atot * 4);
+        } else {
+            // neighbour lists: count the section's directed pixel edges, lay out
+            // its sort buffer (a power of two) and its pool (two halves of
+            // 3 x edges + 64 words), write the edges; sorted below
+            CK(cudaMemsetAsync(h->ccnt.p, 0, 8 * G.nsec, s));
+            k_csr_emit<<<grid_pix, 256, 0, s>>>(g, h->label.p, h->slot_of_id.p, GI[1].p, GI[2].p, lev - 1,
+                                                h->p.connectivity, GJ[0].p, h->ccnt.p, nullptr, nullptr);
+            h->nlaunch++;
+            std::vector<unsigned long long> cnt(G.nsec);
+            CK(cudaMemcpyAsync(cnt.data(), h->ccnt.p, 8 * G.nsec, cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+            std::vector<int64_t> ebase(G.nsec + 1), epow(G.nsec), pbase(G.nsec + 1), hcap(G.nsec);
+            int64_t et = 0, pt = 0;
+            for (int k = 0; k < G.nsec; k++) {
+                int64_t e2 = 1;
+                while (e2 < (int64_t)cnt[k]) e2 <<= 1;
+                epow[k] = e2;
+                ebase[k] = et;
+                et += e2;
+                hcap[k] = 3 * (int64_t)cnt[k] + 64;
+                if (hcap[k] >= ((int64_t)1 << 31)) return RHSEG_ERANGE;   // offsets are 32-bit
+                pbase[k] = pt;
+                pt += 2 * hcap[k];
+            }
+            ebase[G.nsec] = et;
+            pbase[G.nsec] = pt;
+            if ((rc = h->ckeys.alloc((size_t)et))) return rc;
+            if ((rc = h->nbr.alloc((size_t)pt))) return rc;
+            CK(cudaMemcpyAsync(h->cebase.p, ebase.data(), 8 * (G.nsec + 1), cudaMemcpyHostToDevice, s));
+            CK(cudaMemcpyAsync(h->cepow.p, epow.data(), 8 * G.nsec, cudaMemcpyHostToDevice, s));
+            CK(cudaMemcpyAsync(h->cpbase.p, pbase.data(), 8 * (G.nsec + 1), cudaMemcpyHostToDevice, s));
+            CK(cudaMemcpyAsync(h->chcap.p, hcap.data(), 8 * G.nsec, cudaMemcpyHostToDevice, s));
+            CK(cudaMemsetAsync(h->ccnt.p, 0, 8 * G.nsec, s));
+            k_csr_emit<<<grid_pix, 256, 0, s>>>(g, h->label.p, h->slot_of_id.p, GI[1].p, GI[2].p, lev - 1,
+                                                h->p.connectivity, GJ[0].p, h->ccnt.p, h->cebase.p, h->ckeys.p);
+            h->nlaunch++;
+            h->stats.adjacency_bytes = std::max<int64_t>(h->stats.adjacency_bytes,
+                                                         et * 8 + pt * 4 + G.roff[G.nsec] * 8);
+        }
         CK(cudaGetLastError());
         LevelDev D{};
         D.level = lev; D.nsec = G.nsec; D.B = h->B; D.Bs = h->Bs; D.Bpad = h->Bpad;
@@ -874,6 +934,10 @@ static int run_impl(rhseg_handle *h)
         D.Af = h->Af.p; D.kf = h->kf.p; D.Ad = h->Ad.p; D.kd = h->kd.p;
         D.H = (h->p.precision == 1 || h->p.precision == 2) ? h->H.p : nullptr;
         D.adj = h->adj.p; D.cand = h->cand.p; D.cand_cap = cand_cap;
+        if (csr) {
+            D.csr = 1;
+            D.nbr = h->nbr.p; D.pbase = h->cpbase.p; D.hcap = h->chcap.p; D.nofs = h->nofs.p; D.ndeg = h->ndeg.p;
+        }
         if (h->qf.p && h->p.spclust_wght > 0.0 && !inc) {
             D.candg = h->candg.p; D.qf = h->qf.p;
             D.err_gamma = sc.gamma; D.err_u = sc.u; D.err_etaB = sc.eta * std::sqrt((double)h->B);
@@ -896,6 +960,10 @@ static int run_impl(rhseg_handle *h)
             D.sinit = h->sinit.p; D.sT = h->sT.p; D.ckey = h->ckey.p;
             D.sE = h->sE.p; D.sk = h->sk.p; D.inc_onepg = sc.onepg_f; D.sbuf = h->sbuf.p;
             D.srowx = h->srowx.p; D.sinfo = h->sinfo.p;
+        }
+        if (csr) {
+            k_csr_build<<<G.nsec, 1024, 0, s>>>(D, h->ccnt.p, h->cebase.p, h->cepow.p, h->ckeys.p);
+            h->nlaunch++;
         }
         k_init_best<<<dim3(std::max(1, std::min(64, ceil_div(m0max, 8))), G.nsec), 256, 0, s>>>(D); h->nlaunch++;
         int32_t target = (lev == 1) ? h->p.conv_nregions : h->min_nr;
@@ -943,7 +1011,9 @@ static int run_impl(rhseg_handle *h)
         auto enqueue_chunk = [&]() -> int {
             for (int k = 0; k < chunk; k++) {
                 if (prof) CK(cudaEventRecord(h->prof_ev[(0 * chunk + k) * 2], s));
-                k_adj_step<<<G.nsec, STEP_THREADS, 0, s>>>(D, sc); h->nlaunch++;
+                if (csr) k_adj_step<true><<<G.nsec, STEP_THREADS, 0, s>>>(D, sc);
+                else k_adj_step<false><<<G.nsec, STEP_THREADS, 0, s>>>(D, sc);
+                h->nlaunch++;
                 if (prof) CK(cudaEventRecord(h->prof_ev[(0 * chunk + k) * 2 + 1], s));
                 if (h->p.spclust_wght > 0.0) {
                     if (prof) CK(cudaEventRecord(h->prof_ev[(1 * chunk + k) * 2], s));
@@ -951,7 +1021,8 @@ static int run_impl(rhseg_handle *h)
                     else launch_screen(h, D, s);
                     if (prof) CK(cudaEventRecord(h->prof_ev[(1 * chunk + k) * 2 + 1], s));
                     if (inc) k_spec_inc<<<G.nsec, STEP_THREADS, 0, s>>>(D, sc);
-                    else k_spec_step<<<G.nsec, STEP_THREADS, 0, s>>>(D, sc);
+                    else if (csr) k_spec_step<true><<<G.nsec, STEP_THREADS, 0, s>>>(D, sc);
+                    else k_spec_step<false><<<G.nsec, STEP_THREADS, 0, s>>>(D, sc);
                     h->nlaunch++;
                     k_write_rows<<<h->n_sm * 4, 256, 0, s>>>(D, sc, 1); h->nlaunch++;
                     if (prof) CK(cudaEventRecord(h->prof_ev[(2 * chunk + k) * 2 + 1], s));
@@ -1376,6 +1447,8 @@ extern "C" void rhseg_destroy(rhseg_handle *h)
     h->srowx.release(); h->sinfo.release();
     h->candg.release(); h->qf.release();
     h->slot_of_pos.release(); h->X.release(); h->Af.release(); h->kf.release(); h->H.release(); h->Ad.release(); h->kd.release();
+    h->nbr.release(); h->nofs.release(); h->ndeg.release(); h->ckeys.release(); h->ccnt.release();
+    h->cebase.release(); h->cepow.release(); h->cpbase.release(); h->chcap.release();
     h->adj.release(); h->aoff.release(); h->Wrow.release(); h->ref.release(); h->cand.release(); h->st.release();
     h->log.release(); h->err.release(); h->active.release(); h->wlist.release(); h->wcount.release();
     h->S0.release(); h->n0.release();

@@ -45,7 +45,9 @@ struct SecState {
     uint32_t err_rel_bits, err_bnd_bits;
     int64_t err_pairs;     // re-checked pairs the two maxima cover
     int32_t ranges_stale;  // the kept norm ranges of the position blocks need a full recompute
-    int32_t pad2;
+    int32_t ptop;          // CSR adjacency: words in use in the current half of the section's pool
+    int32_t phalf;         // CSR adjacency: the half of the pool in use (0 or 1)
+    int32_t pad3;
 };
 
 // Geometry and buffers of the level in flight (device pointers).  Arrays
@@ -83,6 +85,15 @@ struct LevelDev {
     double  *Ad;  double *kd;  // screen row terms (precision 0)
     // adjacency bitmaps
     uint32_t *adj;
+    // CSR adjacency (csr = 1; the bitmap fields are then unused): slot r's
+    // neighbour slots, sorted ascending, at nbr[pbase[k] + phalf * hcap[k] +
+    // nofs[r]], ndeg[r] of them; each section's pool has two halves of
+    // hcap[k] words, used in turn by the compaction
+    int32_t csr;
+    int32_t *nbr;
+    const int64_t *pbase;
+    const int64_t *hcap;
+    int32_t *nofs, *ndeg;
     // candidates
     uint32_t *cand;            // [nsec][cand_cap][2] positions
     int64_t cand_cap;

@@ -813,7 +813,7 @@ __global__ void __launch_bounds__(STEP_THREADS, 2) k_spec_inc(LevelDev L, Screen
     int merged = 0;
     if (best.k != RHSEG_KEY_NONE && best.k < tbits) {      // K < t (non-negative binary64)
         const int a = (int)best.lo, b = (int)best.hi;
-        block_merge(L, sec, st, a, b, __longlong_as_double((long long)best.k), 1, sc, sm);
+        block_merge<false>(L, sec, st, a, b, __longlong_as_double((long long)best.k), 1, sc, sm);
         merged = 1;
         if (threadIdx.x == 0) {
             st.pm_a[st.npm] = a;

@@ -8,7 +8,9 @@
 //              the order kept whenever the live count drops below a
 //              128-position block boundary;
 //   adjacency  one dense bitmap per section, m0 x W words (W = ceil(m0/32)
-//              rounded to 4), symmetric, no self bits;
+//              rounded to 4), symmetric, no self bits; or (L.csr) sorted
+//              neighbour lists per slot in a per-section pool
+//              (rhseg_csr.cuh);
 //   bestK/P    per slot: the smallest (K, pair) over its adjacent partners
 //              (kept exact and current after every merge);
 //   log        one segment per (level, section);
@@ -45,6 +47,10 @@ __device__ __forceinline__ int32_t morton2(int32_t rb, int32_t cb, int nbits)
     }
     return s;
 }
+
+}  // namespace rhseg
+#include "rhseg_csr.cuh"
+namespace rhseg {
 
 // ---------------------------------------------------------------------------
 // Level set-up
@@ -221,7 +227,17 @@ __global__ void k_init_best(LevelDev L)
         PairKey best = pk_none();
         const int64_t *Si = L.S + (ro + i) * L.Bs;
         int64_t ni = L.n[ro + i];
-        for (int w = 0; w < W; w++) {
+        if (L.csr) {
+            int d;
+            const int32_t *lst = csr_row(L, sec, 0, ro, i, d);
+            for (int e = 0; e < d; e++) {
+                const int r = lst[e];
+                double K = warp_key(Si, ni, L.S + (ro + r) * L.Bs, L.n[ro + r], L.B, L.err);
+                PairKey c = pk_make(dbits(K), i, r);
+                if (pk_less(c, best)) best = c;
+            }
+        }
+        for (int w = 0; w < (L.csr ? 0 : W); w++) {
             uint32_t bits = row[w];
             while (bits) {
                 int r = w * 32 + __ffs(bits) - 1;
@@ -421,7 +437,11 @@ __global__ void __launch_bounds__(STEP_THREADS) k_init_section(LevelDev L, Scree
     const uint32_t *A = L.adj + L.aoff[sec];
     int W = L.W[sec];
     long long pc = 0;
-    for (int64_t w = threadIdx.x; w < (int64_t)m0 * W; w += blockDim.x) pc += __popc(A[w]);
+    if (L.csr) {
+        for (int i = threadIdx.x; i < m0; i += blockDim.x) pc += L.ndeg[L.roff[sec] + i];
+    } else {
+        for (int64_t w = threadIdx.x; w < (int64_t)m0 * W; w += blockDim.x) pc += __popc(A[w]);
+    }
     pc = block_sum_ll(pc, red);
     __syncthreads();
     (void)sc;    // operand rows are written by k_write_rows (rows_from = m0)
@@ -549,15 +569,26 @@ __device__ __forceinline__ void set_best(const LevelDev &L, int64_t ro, int r, u
 
 // Exact best adjacent partner of slot r recomputed by one warp (the row's
 // words are read by the lanes, set bits visited in order, one key per bit).
-__device__ void warp_rescan_row(const LevelDev &L, int sec, int r)
+template <bool CSR>
+__device__ void warp_rescan_row(const LevelDev &L, int sec, int r, int phalf)
 {
     const int lane = threadIdx.x & 31;
     const int64_t ro = L.roff[sec];
-    const int W = L.W[sec];
-    const uint32_t *row = L.adj + L.aoff[sec] + (int64_t)r * W;
+    const int W = CSR ? 0 : L.W[sec];
+    const uint32_t *row = L.adj + (CSR ? 0 : L.aoff[sec]) + (int64_t)r * W;
     const int64_t *Sr = L.S + (ro + r) * L.Bs;
     const int64_t nr = L.n[ro + r];
     PairKey best = pk_none();
+    if (CSR) {                                     // lists: one key per entry
+        int d;
+        const int32_t *lst = csr_row(L, sec, phalf, ro, r, d);
+        for (int e = 0; e < d; e++) {
+            const int q = lst[e];
+            double K = warp_key(Sr, nr, L.S + (ro + q) * L.Bs, L.n[ro + q], L.B, L.err);
+            PairKey c = pk_make(dbits(K), r, q);
+            if (pk_less(c, best)) best = c;
+        }
+    }
     for (int w0 = 0; w0 < W; w0 += 32) {
         uint32_t word = (w0 + lane < W) ? row[w0 + lane] : 0u;
         unsigned nz = __ballot_sync(0xffffffffu, word != 0);
@@ -583,27 +614,36 @@ __device__ void warp_rescan_row(const LevelDev &L, int sec, int r)
 // Best adjacent partners after merging b into a, when the batched lists do
 // not fit: the merged row by warps over its neighbours, re-scans one warp
 // per row.
+template <bool CSR>
 __device__ void block_best_update_slow(const LevelDev &L, int sec, int a, int b, StepSmem &sm)
 {
     const int64_t ro = L.roff[sec];
-    const int W = L.W[sec];
-    const uint32_t *rowA = L.adj + L.aoff[sec] + (int64_t)a * W;
+    const int W = CSR ? 0 : L.W[sec];
+    const uint32_t *rowA = L.adj + (CSR ? 0 : L.aoff[sec]) + (int64_t)a * W;
+    int dA = 0;
+    const int32_t *lstA = CSR ? csr_row(L, sec, sm.st.phalf, ro, a, dA) : nullptr;
     const int tid = threadIdx.x, nt = blockDim.x, wid = tid >> 5, nw = nt >> 5, lane = tid & 31;
     const int64_t *Sa = L.S + (ro + a) * L.Bs;
     const int64_t na = L.n[ro + a];
     PairKey best = pk_none();
     // neighbours of a: their key with a; rows whose best partner was a or b
-    // are re-scanned afterwards (listed in sm.nb, processed per chunk)
-    for (int w0 = 0; w0 < W; w0 += NB_CHUNK_WORDS) {
+    // are re-scanned afterwards (listed in sm.nb, processed per chunk of
+    // bitmap words, or of list entries)
+    const int nunit = CSR ? dA : W, ustep = CSR ? NB_CHUNK_WORDS * 32 : NB_CHUNK_WORDS;
+    for (int w0 = 0; w0 < nunit; w0 += ustep) {
         __syncthreads();
         if (tid == 0) sm.nnb = 0;
         __syncthreads();
-        for (int w = w0 + tid; w < min(W, w0 + NB_CHUNK_WORDS); w += nt) {
-            uint32_t bits = rowA[w];
-            while (bits) {
-                int q = w * 32 + __ffs(bits) - 1;
-                bits &= bits - 1;
-                sm.nb[atomicAdd(&sm.nnb, 1)] = q;
+        if (CSR) {
+            for (int e = w0 + tid; e < min(dA, w0 + ustep); e += nt) sm.nb[atomicAdd(&sm.nnb, 1)] = lstA[e];
+        } else {
+            for (int w = w0 + tid; w < min(W, w0 + NB_CHUNK_WORDS); w += nt) {
+                uint32_t bits = rowA[w];
+                while (bits) {
+                    int q = w * 32 + __ffs(bits) - 1;
+                    bits &= bits - 1;
+                    sm.nb[atomicAdd(&sm.nnb, 1)] = q;
+                }
             }
         }
         __syncthreads();
@@ -621,7 +661,7 @@ __device__ void block_best_update_slow(const LevelDev &L, int sec, int a, int b,
                 if (pk_less(nc, old)) { L.bestK[ro + r] = nc.k; L.bestP[ro + r] = a; }
             }
             __syncwarp();
-            if (rescan) warp_rescan_row(L, sec, r);
+            if (rescan) warp_rescan_row<CSR>(L, sec, r, sm.st.phalf);
         }
     }
     best = block_min_pk(best, sm.pk);
@@ -634,16 +674,18 @@ __device__ void block_best_update_slow(const LevelDev &L, int sec, int a, int b,
 
 // Merge slot b into slot a (a < b, so a keeps the smaller ID).  Whole block;
 // st is the block's shared copy of the section state.
+template <bool CSR>
 __device__ void block_merge(const LevelDev &L, int sec, SecState &st, int a, int b, double K, int kind,
                             const ScreenConst &sc, StepSmem &sm)
 {
     const int64_t ro = L.roff[sec];
-    const int W = L.W[sec];
-    uint32_t *A = L.adj + L.aoff[sec];
+    constexpr bool csr = CSR;
+    const int W = csr ? 0 : L.W[sec];
+    uint32_t *A = L.adj + (csr ? 0 : L.aoff[sec]);
     uint32_t *rowA = A + (int64_t)a * W;
     uint32_t *rowB = A + (int64_t)b * W;
     const int tid = threadIdx.x, nt = blockDim.x, wid = tid >> 5;
-    const int ab = (rowA[b >> 5] >> (b & 31)) & 1;
+    int ab = csr ? 0 : (int)((rowA[b >> 5] >> (b & 31)) & 1);
     long long pa = 0, pb = 0;
     for (int w = tid; w < W; w += nt) { pa += __popc(rowA[w]); pb += __popc(rowB[w]); }
     pa = block_sum_ll(pa, sm.ll);
@@ -672,30 +714,40 @@ __device__ void block_merge(const LevelDev &L, int sec, SecState &st, int a, int
         ((rhseg_merge *)L.log)[L.loff[sec] + st.log_n] = m;
         st.log_n += 1;
     }
-    // adjacency: row a |= row b, neighbours of b now point to a
-    for (int w = tid; w < W; w += nt) rowA[w] |= rowB[w];
-    __syncthreads();
-    if (tid == 0) {
-        rowA[a >> 5] &= ~(1u << (a & 31));
-        rowA[b >> 5] &= ~(1u << (b & 31));
-    }
-    for (int w = tid; w < W; w += nt) {
-        uint32_t bits = rowB[w];
-        while (bits) {
-            int r = w * 32 + __ffs(bits) - 1;
-            bits &= bits - 1;
-            if (r == a) continue;
-            uint32_t *rowR = A + (int64_t)r * W;
-            atomicOr(&rowR[a >> 5], 1u << (a & 31));
-            atomicAnd(&rowR[b >> 5], ~(1u << (b & 31)));
-        }
-    }
-    __syncthreads();
-    for (int w = tid; w < W; w += nt) rowB[w] = 0;
-    __syncthreads();
     long long pn = 0;
-    for (int w = tid; w < W; w += nt) pn += __popc(rowA[w]);
-    pn = block_sum_ll(pn, sm.ll);
+    int dA = 0;
+    const int32_t *lstA = nullptr;
+    if (csr) {
+        // lists: a's union at the top of the pool, b replaced by a elsewhere
+        int ipa, ipb, iab, ipn;
+        csr_merge(L, sec, st, a, b, ipa, ipb, iab, ipn);
+        pa = ipa; pb = ipb; ab = iab; pn = ipn;
+        lstA = csr_row(L, sec, st.phalf, ro, a, dA);
+    } else {
+        // adjacency: row a |= row b, neighbours of b now point to a
+        for (int w = tid; w < W; w += nt) rowA[w] |= rowB[w];
+        __syncthreads();
+        if (tid == 0) {
+            rowA[a >> 5] &= ~(1u << (a & 31));
+            rowA[b >> 5] &= ~(1u << (b & 31));
+        }
+        for (int w = tid; w < W; w += nt) {
+            uint32_t bits = rowB[w];
+            while (bits) {
+                int r = w * 32 + __ffs(bits) - 1;
+                bits &= bits - 1;
+                if (r == a) continue;
+                uint32_t *rowR = A + (int64_t)r * W;
+                atomicOr(&rowR[a >> 5], 1u << (a & 31));
+                atomicAnd(&rowR[b >> 5], ~(1u << (b & 31)));
+            }
+        }
+        __syncthreads();
+        for (int w = tid; w < W; w += nt) rowB[w] = 0;
+        __syncthreads();
+        for (int w = tid; w < W; w += nt) pn += __popc(rowA[w]);
+        pn = block_sum_ll(pn, sm.ll);
+    }
     if (tid == 0) {
         st.nadj = st.nadj - pa - pb + ab + pn;
         sm.npair = 0;
@@ -706,6 +758,11 @@ __device__ void block_merge(const LevelDev &L, int sec, SecState &st, int a, int
     __syncthreads();
     // ---- exact best partners: one batched key phase ----
     // entries of row 0: (a, r) for every neighbour r of a
+    for (int e = tid; e < dA; e += nt) {
+        int idx = atomicAdd(&sm.npair, 1);
+        if (idx < PAIR_CAP) { sm.pi[idx] = a; sm.pj[idx] = lstA[e]; sm.prow[idx] = 0; }
+        else sm.overflow = 1;
+    }
     for (int w = tid; w < W; w += nt) {
         uint32_t bits = rowA[w];
         while (bits) {
@@ -730,7 +787,20 @@ __device__ void block_merge(const LevelDev &L, int sec, SecState &st, int a, int
         }
         __syncthreads();
         const int nr = min(sm.nrows, ROW_CAP);
-        if (!sm.overflow) {
+        if (!sm.overflow && csr) {
+            const int lane = tid & 31, nw = nt >> 5;
+            for (int k = 1 + wid; k < nr; k += nw) {
+                const int r = sm.rows[k];
+                int dr;
+                const int32_t *lr = csr_row(L, sec, st.phalf, ro, r, dr);
+                for (int e = lane; e < dr; e += 32) {
+                    int idx = atomicAdd(&sm.npair, 1);
+                    if (idx < PAIR_CAP) { sm.pi[idx] = r; sm.pj[idx] = lr[e]; sm.prow[idx] = (int16_t)k; }
+                    else sm.overflow = 1;
+                }
+            }
+        }
+        if (!sm.overflow && !csr) {
             for (int64_t f = tid; f < (int64_t)(nr - 1) * W; f += nt) {
                 const int k = 1 + (int)(f / W), w = (int)(f % W);
                 const int r = sm.rows[k];
@@ -747,7 +817,7 @@ __device__ void block_merge(const LevelDev &L, int sec, SecState &st, int a, int
         __syncthreads();
     }
     if (sm.overflow) {
-        block_best_update_slow(L, sec, a, b, sm);
+        block_best_update_slow<CSR>(L, sec, a, b, sm);
     } else {
         const int np = sm.npair, nr = sm.nrows;
         for (int k = tid; k < nr; k += nt) { sm.rowK[k] = RHSEG_KEY_NONE; sm.rowT[k] = ~0ull; }
@@ -809,6 +879,7 @@ __device__ void block_merge(const LevelDev &L, int sec, SecState &st, int a, int
 // bK / bP: the stage's per-slot best (bP < 0 or bK = RHSEG_KEY_NONE: none).
 // Returns the merges done (uniform over the block); *kfirst = the first
 // one's key, the stage's smallest.
+template <bool CSR>
 __device__ int block_merge_mutual(const LevelDev &L, int sec, SecState &st, const uint64_t *bK,
                                   const int32_t *bP, int kind, const ScreenConst &sc, StepSmem &sm,
                                   double *kfirst)
@@ -857,7 +928,7 @@ __device__ int block_merge_mutual(const LevelDev &L, int sec, SecState &st, cons
         const unsigned long long kb = list[2 * e], t = list[2 * e + 1];
         const double K = __longlong_as_double((long long)kb);
         if (e == 0) *kfirst = K;
-        block_merge(L, sec, st, (int)(t >> 32), (int)(t & 0xffffffffu), K, kind, sc, sm);
+        block_merge<CSR>(L, sec, st, (int)(t >> 32), (int)(t & 0xffffffffu), K, kind, sc, sm);
         done++;
     }
     __syncthreads();
@@ -1286,6 +1357,7 @@ __global__ void __launch_bounds__(STEP_THREADS) k_sort_positions(LevelDev L)
 }
 
 // Step 2 of HSEG: merge the adjacent pair of minimum key.
+template <bool CSR>
 __global__ void __launch_bounds__(STEP_THREADS, 2) k_adj_step(LevelDev L, ScreenConst sc)
 {
     const int sec = blockIdx.x;
@@ -1335,10 +1407,10 @@ __global__ void __launch_bounds__(STEP_THREADS, 2) k_adj_step(LevelDev L, Screen
         // reading R12: every mutually best adjacent pair; the threshold of the
         // spectral stage comes from the first (smallest) of them
         double k0;
-        if (block_merge_mutual(L, sec, st, L.bestK, L.bestP, 0, sc, sm, &k0) > 0) { merged = 1; Kadj = k0; }
+        if (block_merge_mutual<CSR>(L, sec, st, L.bestK, L.bestP, 0, sc, sm, &k0) > 0) { merged = 1; Kadj = k0; }
     } else if (best.k != RHSEG_KEY_NONE) {
         Kadj = __longlong_as_double((long long)best.k);
-        block_merge(L, sec, st, (int)best.lo, (int)best.hi, Kadj, 0, sc, sm);
+        block_merge<CSR>(L, sec, st, (int)best.lo, (int)best.hi, Kadj, 0, sc, sm);
         merged = 1;
         if (L.incremental && threadIdx.x == 0) {      // rows to recompute for the spectral minima
             st.pm_a[st.npm] = (int)best.lo;
@@ -1443,6 +1515,7 @@ __device__ void block_screen_error(const LevelDev &L, int sec, SecState &st, con
 // non-adjacent pair when no finite threshold exists or the candidate buffer
 // overflowed), merge of the minimum if below the threshold; then, when
 // enough regions died, a new compact position list for the screen.
+template <bool CSR>
 __global__ void __launch_bounds__(STEP_THREADS, 2) k_spec_step(LevelDev L, ScreenConst sc)
 {
     const int sec = blockIdx.x;
@@ -1454,8 +1527,9 @@ __global__ void __launch_bounds__(STEP_THREADS, 2) k_spec_step(LevelDev L, Scree
     if (!st.spec_pending) return;
     const int64_t ro = L.roff[sec];
     const int m0 = st.m0;
-    const int W = L.W[sec];
-    const uint32_t *A = L.adj + L.aoff[sec];
+    constexpr bool csr = CSR;
+    const int W = csr ? 0 : L.W[sec];
+    const uint32_t *A = L.adj + (csr ? 0 : L.aoff[sec]);
     const double t = st.tthr;
     const int count = st.count;
     const int mc = st.mc;
@@ -1485,7 +1559,8 @@ __global__ void __launch_bounds__(STEP_THREADS, 2) k_spec_step(LevelDev L, Scree
                 for (uint32_t c = c0 + tid; c < min(ncand, c0 + PAIR_CAP); c += nt) {
                     const int i = sop[cand[2 * c]], j = sop[cand[2 * c + 1]];
                     if (i == j || !L.alive[ro + i] || !L.alive[ro + j]) continue;
-                    if ((A[(int64_t)i * W + (j >> 5)] >> (j & 31)) & 1) continue;
+                    if (csr ? csr_adjacent(L, sec, st.phalf, ro, i, j) : ((A[(int64_t)i * W + (j >> 5)] >> (j & 31)) & 1))
+                        continue;
                     const int idx = atomicAdd(&sm.npair, 1);
                     sm.pi[idx] = min(i, j);
                     sm.pj[idx] = max(i, j);
@@ -1525,7 +1600,8 @@ __global__ void __launch_bounds__(STEP_THREADS, 2) k_spec_step(LevelDev L, Scree
                 while ((i + 1) * (2 * m0 - i - 2) / 2 <= e) i++;
                 const int64_t j = e - i * (2 * m0 - i - 1) / 2 + i + 1;
                 if (!L.alive[ro + i] || !L.alive[ro + j]) continue;
-                if ((A[i * W + (j >> 5)] >> (j & 31)) & 1) continue;
+                if (csr ? csr_adjacent(L, sec, st.phalf, ro, (int)i, (int)j) : ((A[i * W + (j >> 5)] >> (j & 31)) & 1))
+                    continue;
                 const double K = warp_key(L.S + (ro + i) * L.Bs, L.n[ro + i], L.S + (ro + j) * L.Bs, L.n[ro + j], L.B, L.err);
                 if (!(K < t)) continue;
                 const uint64_t kb = dbits(K);
@@ -1558,9 +1634,9 @@ __global__ void __launch_bounds__(STEP_THREADS, 2) k_spec_step(LevelDev L, Scree
     int merged = 0;
     if (L.multi) {
         double k0;
-        merged = block_merge_mutual(L, sec, st, L.mK, (const int32_t *)L.mP, 1, sc, sm, &k0) > 0;
+        merged = block_merge_mutual<CSR>(L, sec, st, L.mK, (const int32_t *)L.mP, 1, sc, sm, &k0) > 0;
     } else if (best.k != RHSEG_KEY_NONE) {
-        block_merge(L, sec, st, (int)best.lo, (int)best.hi, __longlong_as_double((long long)best.k), 1, sc, sm);
+        block_merge<CSR>(L, sec, st, (int)best.lo, (int)best.hi, __longlong_as_double((long long)best.k), 1, sc, sm);
         merged = 1;
     }
     __syncthreads();

@@ -21,7 +21,9 @@ pipeline waits in clock cycles, 0 = the default of about 2 s; a wait that
 runs out makes run() raise RHSEGError with code RHSEG_ETIMEOUT); screen_group
 (K slices per tcgen05.commit of the tensor-core screen, 0 = default) and
 screen_pair (1: the tensor-core screen as CTA pairs sharing 256x256 tiles),
-both chosen by the autotuner, results identical.
+both chosen by the autotuner, results identical; adjacency (0: a bit matrix per
+section, 1: sorted neighbour lists with memory in proportion to the edges;
+results identical).
 """
 from __future__ import annotations
 
@@ -33,7 +35,8 @@ from . import _abi
 
 DEFAULTS = dict(rnb_levels=1, conv_nregions=1, spclust_wght=0.0, connectivity=8, min_nregions=0,
                 n_out_levels=1, seam_pass=1, precision=1, profile=0, incremental=0,
-                multi_merge=0, wait_cycles=0, screen_group=0, screen_pair=0)
+                multi_merge=0, wait_cycles=0, screen_group=0, screen_pair=0,
+                adjacency=0)
 
 
 class RHSEGError(RuntimeError):

@@ -214,3 +214,82 @@ def test_launch_forms_give_identical_runs(P, orc):
             seg.run(stream=stream)
             _assert_same(seg, ref, f"p{precision} {extra} {'legacy' if stream is not None else 'own'} stream")
             seg.close()
+
+
+# ---------------------------------------------------------------------------
+# Neighbour-list adjacency (adjacency = 1): the same merges as the oracle, with
+# memory in proportion to the region edges.
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("precision", [1, 3])
+def test_csr_adjacency_tiny_cases_with_ties(P, orc, precision):
+    for ci, case in enumerate(BRUTE_CASES):
+        rows, cols, B, maxval, mask_p, L, w, conv, conn, min_nr, n_out, seam = case
+        for seed in (1, 2):
+            img, mask = synth.random_cube(seed * 101 + rows * 7 + cols, rows, cols, B, maxval, mask_p)
+            kw = dict(rnb_levels=L, spclust_wght=w, conv_nregions=conv, connectivity=conn,
+                      min_nregions=min_nr, n_out_levels=n_out, seam_pass=seam)
+            _assert_same(_run(P, img, mask, precision=precision, adjacency=1, **kw), orc.run(img, mask, **kw),
+                         f"csr case {ci} s{seed}")
+
+
+@pytest.mark.parametrize("si", range(len(SCENES)))
+def test_csr_adjacency_scenes(P, orc, si):
+    rows, cols, B, L, w, conv, conn, min_nr, n_out, seam, masked = SCENES[si]
+    img, mask = synth.make(4 if masked else 2, seed=400 + si, rows=rows, cols=cols)
+    img = np.ascontiguousarray(img[:, :, :B])
+    kw = dict(rnb_levels=L, spclust_wght=w, conv_nregions=conv, connectivity=conn, min_nregions=min_nr,
+              n_out_levels=n_out, seam_pass=seam)
+    _assert_same(_run(P, img, mask, precision=1, adjacency=1, **kw), orc.run(img, mask, **kw), f"csr scene {si}")
+
+
+def test_csr_adjacency_edge_cases_and_multi_merge(P, orc):
+    rng = np.random.default_rng(3)
+    img = rng.integers(0, 100, (5, 7, 3)).astype(np.uint16)
+    m = np.zeros((5, 7), np.uint8)
+    m[:, 3] = 1
+    m[2, :] = 1
+    cases = [(img, np.ones((5, 7), np.uint8), dict(rnb_levels=2, conv_nregions=2)),
+             (img[:1, :1], None, dict(rnb_levels=1, conv_nregions=1)),
+             (img, None, dict(rnb_levels=6, conv_nregions=3, spclust_wght=0.5)),
+             (img[:1], None, dict(rnb_levels=3, conv_nregions=1, spclust_wght=1.0)),
+             (img, m, dict(rnb_levels=1, conv_nregions=1, spclust_wght=0.7)),
+             (img, m, dict(rnb_levels=1, conv_nregions=1, spclust_wght=0.0)),
+             (np.full((6, 6, 2), 65535, np.uint16), None, dict(rnb_levels=2, conv_nregions=1, spclust_wght=1.0))]
+    for i, (im, mk, kw) in enumerate(cases):
+        _assert_same(_run(P, im, mk, precision=1, adjacency=1, **kw), orc.run(im, mk, **kw), f"csr edge {i}")
+    im, mk = synth.make(4, seed=21, rows=40, cols=36)
+    im = np.ascontiguousarray(im[:, :, :8])
+    kw = dict(rnb_levels=2, spclust_wght=0.4, conv_nregions=5, multi_merge=1)
+    _assert_same(_run(P, im, mk, precision=1, adjacency=1, **kw), orc.run(im, mk, **kw), "csr multi-merge")
+
+
+def test_csr_adjacency_compaction_on_a_growing_region(P, orc):
+    """A flat image: one region absorbs its neighbours one by one, so every
+    merge writes a long union and the section's pool is compacted many
+    times over; the merges still equal the oracle's."""
+    img = np.full((48, 48, 2), 1000, np.uint16)
+    img[::7, ::5, 1] += 3                           # a few ties broken
+    for kw in (dict(rnb_levels=1, conv_nregions=1, spclust_wght=0.0),
+               dict(rnb_levels=1, conv_nregions=3, spclust_wght=0.5, connectivity=4)):
+        _assert_same(_run(P, img, None, precision=1, adjacency=1, **kw), orc.run(img, None, **kw), f"csr flat {kw}")
+
+
+def test_csr_adjacency_memory_follows_the_edges(P):
+    """One 256x256 section (L = 1): the bit matrix needs m0^2 / 8 bytes
+    (512 MB here), the lists a constant per pixel; identical results."""
+    img, mask = synth.make(2, seed=77, rows=256, cols=256)
+    img = np.ascontiguousarray(img[:, :, :4])
+    kw = dict(rnb_levels=1, spclust_wght=0.0, conv_nregions=64, connectivity=8)
+    a = _run(P, img, mask, precision=1, **kw)
+    b = _run(P, img, mask, precision=1, adjacency=1, **kw)
+    assert np.array_equal(a.log(), b.log())
+    for k in range(a.n_levels()):
+        for x, y in zip(a.level(k), b.level(k)):
+            assert np.array_equal(x, y)
+    ba, bb = a.stats()["adjacency_bytes"], b.stats()["adjacency_bytes"]
+    m0 = int((mask == 0).sum()) if mask is not None else 256 * 256
+    assert ba >= m0 * m0 // 8
+    # at most 8 directed edges per pixel: sort buffer <= 2 x 8 bytes, pools 2 x 3 words, slot offsets
+    assert bb <= 256 * 256 * (8 * (16 + 24) + 8) + 1024, bb
+    assert bb * 10 < ba
