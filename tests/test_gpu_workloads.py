@@ -64,10 +64,10 @@ def _gpu_digest(seg):
     return _digest.result_digest(seg.log(), levels, seg.stats())
 
 
-@pytest.mark.parametrize("k,precision", [(4, 1), (4, 2), (5, 1)])
-def test_full_run_equals_oracle(P, k, precision):
+@pytest.mark.parametrize("k,precision,adjacency", [(4, 1, 0), (4, 2, 0), (5, 1, 0), (4, 1, 1)])
+def test_full_run_equals_oracle(P, k, precision, adjacency):
     """Every record, level and counter of a whole run at full size against the
-    oracle's stored digests."""
+    oracle's stored digests (bit-matrix adjacency, and the neighbour lists)."""
     w = synth.WORKLOADS[k]
     path = os.path.join(GOLDEN, f"full_run_{w.name}.json")
     if not os.path.exists(path):
@@ -76,12 +76,12 @@ def test_full_run_equals_oracle(P, k, precision):
     img, mask = synth.make(k)
     kw = dict(w.params, precision=precision)
     assert want["params"] == {a: b for a, b in kw.items() if a != "precision"}
-    seg = P.RHSEG(img, mask, **kw)
+    seg = P.RHSEG(img, mask, adjacency=adjacency, **kw)
     seg.run()
     got = _gpu_digest(seg)
     seg.close()
     diff = _digest.first_difference(want, got)
-    assert diff == "", f"{w.name} p{precision}: {diff}"
+    assert diff == "", f"{w.name} p{precision} adjacency {adjacency}: {diff}"
 
 
 @pytest.fixture(scope="module")
