@@ -114,6 +114,8 @@ def test_param_validation_needs_no_device(so_path):
     img = (C.c_uint16 * 4)()
     for bad in [dict(spclust_wght=1.5), dict(connectivity=6), dict(rnb_levels=0), dict(rnb_levels=7),
                 dict(precision=9), dict(conv_nregions=0), dict(incremental=1, precision=1),
-                dict(multi_merge=2), dict(multi_merge=1, incremental=1, precision=3)]:
+                dict(multi_merge=2), dict(multi_merge=1, incremental=1, precision=3),
+                dict(wait_cycles=-1), dict(screen_group=9), dict(screen_pair=2), dict(adjacency=2),
+                dict(adjacency=1, incremental=1, precision=3)]:
         p = make_params(**bad)
         assert L.rhseg_create(img, 2, 2, 1, None, C.byref(p), None, C.byref(h)) == _abi.RHSEG_EINVAL
