@@ -359,7 +359,9 @@ def main():
                 "kernel": {1: "screen_simt<f64>", 2: "screen_simt<f32 accumulate>",
                            3: "screen_tcgen05_cta_pair" if params.get("screen_pair") else "screen_tcgen05"}.get(impl, "none"),
                 "launches": scr_n, "avg_launch_ms": scr_ms / max(scr_n, 1),
-                "share_of_run": scr_ms / run_ms if run_ms else None, "peak_source": peak_note}
+                "share_of_run": scr_ms / run_ms if run_ms else None, "peak_source": peak_note,
+                "achieved_useful": (achieved * sum(s.get("screen_useful", 0) for s in stats) / scr_eval
+                                    if scr_eval > 0 else None)}
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -382,7 +384,11 @@ def main():
                    "candidates_below_threshold": stats[-1]["candidates_below"],
                    "fallbacks": stats[-1]["fallbacks"],
                    "evaluated_pairs": stats[-1].get("screen_evaluated", 0),
-                   "useful_over_covered": stats[-1]["screened_pairs"] / max(1, stats[-1].get("screen_evaluated", 0)),
+                   # the method's pairs per pair the MMAs covered (> 1: skipped units count as screened)
+                   "screened_over_covered": stats[-1]["screened_pairs"] / max(1, stats[-1].get("screen_evaluated", 0)),
+                   # of the covered pairs, those (i, j), i < j, of positions in use; the rest is the lower
+                   # triangle of diagonal units and the rows past the last position
+                   "useful_fraction_of_covered": stats[-1].get("screen_useful", 0) / max(1, stats[-1].get("screen_evaluated", 0)),
                    "error_vs_exact": {"max_rel": stats[-1]["screen_err_rel_max"],
                                       "max_over_bound": stats[-1]["screen_err_bound_max"],
                                       "rechecked_pairs": stats[-1]["screen_err_pairs"]}},

@@ -183,6 +183,11 @@ typedef struct rhseg_stats {
     int64_t adjacency_bytes;  /* largest device memory the region adjacency of one
                                  level took in the last rhseg_run (bit matrices, or
                                  lists, offsets and their build scratch)           */
+    int64_t screen_useful;    /* of screen_evaluated, the pairs (i, j), i < j, of
+                                 positions in use (the rest: the lower triangle of
+                                 diagonal units, rows past the last position, and
+                                 the CTA-pair form's padding halves); counted with
+                                 profile = 1 only, else 0                          */
 } rhseg_stats;
 
 typedef struct rhseg_handle rhseg_handle;

@@ -49,6 +49,7 @@ class Stats(C.Structure):
         ("screen_evaluated", C.c_int64), ("device_allocs", C.c_int64),
         ("screen_err_rel_max", C.c_double), ("screen_err_bound_max", C.c_double), ("screen_err_pairs", C.c_int64),
         ("level_screen_evaluated", C.c_int64 * 6), ("adjacency_bytes", C.c_int64),
+        ("screen_useful", C.c_int64),
     ]
 
 

@@ -948,6 +948,7 @@ static int run_impl(rhseg_handle *h)
             D.nlo = h->nlo.p; D.nhi = h->nhi.p; D.sk = h->sk.p; D.brng = h->brng.p;
             D.ulist = h->ulist.p; D.ucap = ucap; D.sortk = h->sortk.p;
             D.tc_pair = h->p.screen_pair;      // the pair form walks the listed tiles
+            D.count_useful = h->p.profile;     // a diagnostic: a shared atomic per kept unit
         }
         if (h->p.multi_merge) {
             D.multi = 1;
@@ -1124,6 +1125,7 @@ static int run_impl(rhseg_handle *h)
             h->stats.screened_pairs += q.screened;
             h->stats.screen_evaluated += q.evaluated;
             h->stats.level_screen_evaluated[lev - 1] += q.evaluated;
+            h->stats.screen_useful += q.useful;
             h->stats.candidates += q.cands;
             h->stats.candidates_below += q.cands_true;
             h->stats.fallbacks += q.fallbacks;

@@ -48,6 +48,7 @@ struct SecState {
     int32_t ptop;          // CSR adjacency: words in use in the current half of the section's pool
     int32_t phalf;         // CSR adjacency: the half of the pool in use (0 or 1)
     int32_t pad3;
+    int64_t useful;        // of the pairs the kept units cover, those (i, j), i < j, of positions below mc
 };
 
 // Geometry and buffers of the level in flight (device pointers).  Arrays
@@ -107,6 +108,7 @@ struct LevelDev {
     long long wait_cycles;     // bound of the screen's pipeline waits (0: the default)
     int32_t tc_group;          // K slices per tcgen05.commit of the screen (0: the default)
     int32_t tc_pair;           // 1: the screen runs as CTA pairs; ulist then lists unit pairs
+    int32_t count_useful;      // 1 (with per-kernel timing): count the useful pairs of the kept units
     int32_t *wlist;            // [nsec] sections whose positions were rebuilt this iteration
     int32_t *wcount;           // their number
     // incremental spectral minima (null unless that mode is on)

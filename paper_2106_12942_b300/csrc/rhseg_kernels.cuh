@@ -1178,6 +1178,17 @@ __global__ void __launch_bounds__(256) k_write_rows(LevelDev L, ScreenConst sc, 
 // The kept units are listed in order; their count and covered pairs go to st.
 constexpr int UL_MAX_BLOCKS = 512;     // sections of up to 65536 positions skip units; larger keep all
 
+// Pairs (r, c), r < c, with r in [r0, r1) and c in [c0, c1) (closed form).
+__device__ __forceinline__ long long pairs_upper(long long r0, long long r1, long long c0, long long c1)
+{
+    if (r1 <= r0 || c1 <= c0) return 0;
+    const long long n1 = max(0ll, min(r1, c0) - r0);            // rows below every column: all pairs
+    long long s = n1 * (c1 - c0);
+    const long long a = max(r0, c0), e = min(r1, c1 - 1);     // rows inside the column range
+    if (e > a) s += (2 * c1 - 1 - a - e) * (e - a) / 2;         // sum of (c1 - 1 - r), r in [a, e)
+    return s;
+}
+
 __device__ void block_unit_list(const LevelDev &L, int sec, SecState &st, float Tf)
 {
     const int mc = st.mc;
@@ -1188,6 +1199,7 @@ __device__ void block_unit_list(const LevelDev &L, int sec, SecState &st, float 
     __shared__ float blo[UL_MAX_BLOCKS], bhi[UL_MAX_BLOCKS], bkm[UL_MAX_BLOCKS];
     __shared__ int32_t wsum[32];
     __shared__ int32_t base;
+    __shared__ unsigned long long s_useful;
     const bool ranges = nb <= UL_MAX_BLOCKS;
     float4 *brng = (L.brng != nullptr) ? (float4 *)L.brng + (pb >> 7) : nullptr;
     if (ranges && brng != nullptr && !st.ranges_stale) {
@@ -1228,7 +1240,7 @@ __device__ void block_unit_list(const LevelDev &L, int sec, SecState &st, float 
             }
         }
     }
-    if (threadIdx.x == 0) base = 0;
+    if (threadIdx.x == 0) { base = 0; s_useful = 0; }
     __syncthreads();
     // a unit (I, Jp) may hold a pair below the threshold (empty blocks:
     // infinite gap, dropped)
@@ -1278,6 +1290,8 @@ __device__ void block_unit_list(const LevelDev &L, int sec, SecState &st, float 
                     const bool k = I < ni && unit_kept(I, Jp);
                     const unsigned m = __ballot_sync(0xffffffffu, k);
                     if (k) {
+                        if (L.count_useful) atomicAdd(&s_useful, (unsigned long long)pairs_upper(I * 128ll, min(I * 128ll + 128, (long long)mc),
+                                                                             Jp * 256ll, min(Jp * 256ll + 256, (long long)mc)));
                         const int r = c + __popc(m & ((1u << lane) - 1u));
                         const int64_t e = 2 * (b0 + (r >> 1));
                         if (r & 1) ul[e + 1] = I;
@@ -1294,6 +1308,10 @@ __device__ void block_unit_list(const LevelDev &L, int sec, SecState &st, float 
             for (int t = threadIdx.x; t < npairs; t += blockDim.x) {
                 int Ip, Jp;
                 tri_decode(t, nbp, Ip, Jp);
+                for (int hh = 0; hh < 2; hh++)
+                    if (L.count_useful) atomicAdd(&s_useful, (unsigned long long)pairs_upper((2 * Ip + hh) * 128ll,
+                                                                         min((2 * Ip + hh) * 128ll + 128, (long long)mc),
+                                                                         Jp * 256ll, min(Jp * 256ll + 256, (long long)mc)));
                 ul[2 * (int64_t)t] = ((2 * Ip) << 16) | Jp;
                 ul[2 * (int64_t)t + 1] = (2 * Ip + 1 < nb) ? 2 * Ip + 1 : -1;
             }
@@ -1303,6 +1321,7 @@ __device__ void block_unit_list(const LevelDev &L, int sec, SecState &st, float 
             st.ranges_stale = 0;
             st.nunits = npairs;
             st.evaluated += (int64_t)npairs * 256 * 256;
+            st.useful += (int64_t)s_useful;
         }
         return;
     }
@@ -1318,6 +1337,9 @@ __device__ void block_unit_list(const LevelDev &L, int sec, SecState &st, float 
             if (2 * Jp + 1 >= I) {
                 keep = unit_kept(I, Jp) ? 1 : 0;
                 entry = (I << 16) | Jp;
+                if (keep && L.count_useful)
+                    atomicAdd(&s_useful, (unsigned long long)pairs_upper(I * 128ll, min(I * 128ll + 128, (long long)mc),
+                                                                         Jp * 256ll, min(Jp * 256ll + 256, (long long)mc)));
             }
         }
         int incl = keep;
@@ -1335,10 +1357,12 @@ __device__ void block_unit_list(const LevelDev &L, int sec, SecState &st, float 
         if (threadIdx.x == 0) base += tot;
         __syncthreads();
     }
+    if (L.count_useful) __syncthreads();     // uniform
     if (threadIdx.x == 0) {
         st.ranges_stale = 0;
         st.nunits = base;
         st.evaluated += (int64_t)base * 128 * 256;
+        st.useful += (int64_t)s_useful;
     }
 }
 
